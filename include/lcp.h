@@ -1,0 +1,178 @@
+/*
+ * lcp.h - C ABI of the GB300 (sm_103a) library for level-crossing-probability
+ * (LCP) maps of the local divergence of uncertain 2D vector fields.
+ *
+ * Method: Ouermi, Li, Moreland, Pugmire, Johnson, Athawale, "Efficient
+ * Probabilistic Visualization of Local Divergence of 2D Vector Fields with
+ * Independent Gaussian Uncertainty", arXiv 2510.01190.  Sec. 3.1 defines the
+ * per-vertex Gaussian model, the divergence stencil (Eq. 1) and the divergence
+ * Gaussian (Eqs. 2, 3); its last paragraph feeds that Gaussian to the
+ * level-crossing probability of Poethkow et al.  Sec. 3.2 and Sec. 4 define the
+ * classical Monte Carlo estimator used as the baseline.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid      H rows x W columns of vertices, H >= 2 and W >= 2.  Vertex (i, j)
+ *           has i = x = column, j = y = row; 2D arrays are row-major [H][W].
+ * Members   one plane per member and component: element (m, j, i) of u lives at
+ *           u[m * member_stride + j * W + i]; member_stride >= H * W.  u is the
+ *           x component, v the y component.  Element type LCP_F32 or LCP_BF16.
+ * Cells     cell (i, j) has vertices (i,j), (i+1,j), (i,j+1), (i+1,j+1); LCP maps
+ *           are [K][H-1][W-1], isovalue-major.
+ * Masks     mean-field crossing bits (optional, may be NULL): for isovalue k and
+ *           cell row j, ceil((W-1)/32) uint32 words; bit (i % 32) of word i / 32
+ *           is set iff cell (i, j) crosses.  Layout [K][H-1][ceil((W-1)/32)].
+ * Boundary  Eq. 1 uses central differences; on the first/last column (row) the
+ *           library uses the first-order forward/backward difference with step
+ *           dx (dy), as Sec. 3.1 states for the boundary.
+ * Memory    every array argument is a DEVICE pointer owned by the caller unless
+ *           the parameter says "host"; the library allocates no device memory.
+ *           fp32 arrays must be 4-byte aligned, bf16/fp16 2-byte aligned; wider
+ *           vector loads are used automatically when alignment allows.
+ * Streams   every call only validates its arguments and enqueues work on
+ *           `stream`; it returns before the GPU finishes.  Errors found on the
+ *           host return a negative lcp_status and enqueue nothing; the message
+ *           is available from lcp_last_error() on the calling thread.
+ * NaN/Inf   NaN or Inf member values propagate to NaN in the statistics of that
+ *           vertex and in every divergence/LCP value that touches it; they are
+ *           not an error.
+ */
+#ifndef LCP_GB300_H
+#define LCP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* lcp_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    LCP_OK = 0,
+    LCP_ERR_ARG = -1,         /* invalid size, pointer, alignment or option */
+    LCP_ERR_CUDA = -2,        /* a CUDA runtime call failed (launch, attribute, ...) */
+    LCP_ERR_UNSUPPORTED = -3, /* valid request the library does not implement */
+    LCP_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    LCP_ERR_NUMERIC = -5      /* reserved: numerically unusable input */
+} lcp_status;
+
+typedef enum { LCP_F32 = 0, LCP_BF16 = 1, LCP_F16 = 2, LCP_F64 = 3 } lcp_dtype;
+
+typedef enum { LCP_MC_GAUSS = 0, LCP_MC_EMPIRICAL = 1 } lcp_mc_mode;
+
+#define LCP_MAX_ISOVALUES 256 /* K limit of every entry point */
+
+/* Human-readable name of a status code (static storage). */
+const char* lcp_status_string(lcp_status s);
+
+/* Message of the last error returned on the calling thread ("" if none). */
+const char* lcp_last_error(void);
+
+/* Library version as 10000 * major + 100 * minor + patch. */
+int lcp_version(void);
+
+/*
+ * lcp_stats - per-vertex Gaussian model of each component (Sec. 3.1, closing
+ * paragraph: mu-hat and sigma-hat^2 are estimated from the ensemble).
+ *
+ *   mean = (1/M) sum_m x_m,  var = sum_m (x_m - mean)^2 / (M - ddof)
+ *
+ * computed in FP32 as shifted sums about member 0 (one pass over the members).
+ * u, v        members, element type `in_dtype` (LCP_F32 or LCP_BF16)
+ * M, H, W     members (M >= 1, M - ddof >= 1), rows, columns
+ * member_stride  elements between consecutive members (>= H*W)
+ * ddof        0 (population) or 1 (sample variance)
+ * mu_u, var_u, mu_v, var_v   outputs, fp32 [H][W]
+ * Errors: LCP_ERR_ARG for a NULL pointer, H < 2, W < 2, M < 1, M - ddof < 1,
+ * ddof not in {0, 1}, member_stride < H*W, or an unsupported dtype.
+ */
+lcp_status lcp_stats(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
+                     int64_t member_stride, int ddof, float* mu_u, float* var_u, float* mu_v,
+                     float* var_v, lcp_stream_t stream);
+
+/*
+ * lcp_divergence - divergence Gaussian N(mu_d, var_d) at every vertex (Eqs. 2
+ * and 3, Sec. 3.1), with the one-sided boundary rule above:
+ *   mu_d  = (mu_u[i+] - mu_u[i-]) / ((i+ - i-) dx) + (mu_v[j+] - mu_v[j-]) / ((j+ - j-) dy)
+ *   var_d = (var_u[i+] + var_u[i-]) / ((i+ - i-) dx)^2 + (var_v[j+] + var_v[j-]) / ((j+ - j-) dy)^2
+ * with i- = max(i-1, 0), i+ = min(i+1, W-1) (j alike).
+ * Inputs fp32 [H][W] (from lcp_stats); outputs mu_d, var_d fp32 [H][W].
+ * dx, dy > 0 (finite).  Errors: LCP_ERR_ARG for NULL, H < 2, W < 2, dx or dy <= 0.
+ */
+lcp_status lcp_divergence(const float* mu_u, const float* var_u, const float* mu_v,
+                          const float* var_v, int H, int W, double dx, double dy, float* mu_d,
+                          float* var_d, lcp_stream_t stream);
+
+/*
+ * lcp_map - level-crossing probability of every cell (Sec. 3.1, last
+ * paragraph, after Poethkow et al.): with p = P(D < c) = erfc((mu_d - c) /
+ * (sigma_d sqrt 2)) / 2 and q = P(D >= c) at the 4 cell vertices, treated as
+ * independent,
+ *   LCP = 1 - p00 p10 p01 p11 - q00 q10 q01 q11.
+ * A vertex with var_d == 0 has p = [mu_d < c], q = 1 - p.
+ * mu_d, var_d   fp32 [H][W]
+ * iso           HOST array of K isovalues (fp32), 1 <= K <= LCP_MAX_ISOVALUES
+ * lcp_out       [K][H-1][W-1] of `out_dtype` (LCP_F32 or LCP_F16)
+ * mask          optional mean-field crossing bits (layout above) or NULL
+ */
+lcp_status lcp_map(const float* mu_d, const float* var_d, int H, int W, const float* iso, int K,
+                   void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, lcp_stream_t stream);
+
+/*
+ * lcp_fused - lcp_stats -> lcp_divergence -> lcp_map in one kernel pass over
+ * the members: each member byte is read from HBM once; statistics, divergence
+ * and per-vertex probabilities stay on chip.  Same arguments and results as
+ * the three calls in sequence (the mean is kept as member-0 shift plus FP32
+ * offset internally, so it is at least as accurate as the unfused path).
+ * K > 32 is processed in passes of 32 isovalues.
+ */
+lcp_status lcp_fused(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
+                     int64_t member_stride, int ddof, double dx, double dy, const float* iso, int K,
+                     void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, lcp_stream_t stream);
+
+/*
+ * lcp_mc - classical Monte Carlo estimate of the LCP map (Sec. 3.2 and Sec. 4):
+ * every sample is one realisation of the whole field; its divergence (Eq. 1,
+ * same boundary rule) is tested per cell and isovalue, "crossing" meaning
+ * min < c <= max over the 4 vertices; counts[k][j][i] is the number of
+ * crossing samples.  The estimate is counts / n_samples.
+ *
+ * mode LCP_MC_GAUSS      U ~ N(mu_u, var_u), V ~ N(mu_v, var_v) per vertex
+ *                        (fp32 [H][W] inputs; u, v ignored, may be NULL)
+ * mode LCP_MC_EMPIRICAL  U, V drawn uniformly and independently from the M
+ *                        members of their own vertex (u, v, in_dtype, M,
+ *                        member_stride used; statistics ignored, may be NULL)
+ * Random numbers: Philox-4x32-10 (Salmon et al., SC'11) with counter
+ * (j*W + i, t, offset lo, offset hi) and key (seed lo, seed hi) gives 4 words
+ * per vertex and sample pair t; sample 2t uses words 0, 1 and sample 2t+1 words
+ * 2, 3.  GAUSS: Box-Muller on the word pair with U1 = (word >> 8 + 1/2) 2^-24,
+ * z_u = sqrt(-2 ln U1) cos(2 pi U2), z_v = sqrt(-2 ln U1) sin(2 pi U2).
+ * EMPIRICAL: member index = (word * M) >> 32 for u and v respectively.
+ * iso           HOST array of K fp32 isovalues
+ * n_samples     1 <= S <= 2^32 - 1
+ * counts        uint32 [K][H-1][W-1] (required)
+ * lcp_out       optional fp32 [K][H-1][W-1] estimate counts / S, or NULL
+ * Errors: LCP_ERR_ARG also when H*W > 2^32.
+ */
+lcp_status lcp_mc(lcp_mc_mode mode, const float* mu_u, const float* var_u, const float* mu_v,
+                  const float* var_v, const void* u, const void* v, lcp_dtype in_dtype, int M,
+                  int64_t member_stride, int H, int W, double dx, double dy, const float* iso, int K,
+                  int64_t n_samples, uint64_t seed, uint64_t offset, uint32_t* counts,
+                  float* lcp_out, lcp_stream_t stream);
+
+/*
+ * lcp_philox_fill - the Monte Carlo generator's raw words, for testing and
+ * for reproducible inputs: out[4 n + r] = word r of Philox-4x32-10 with counter
+ * (n, c1, offset lo, offset hi) and key (seed lo, seed hi), n in [0, count).
+ * out: uint32 [4 * count] device array; 0 <= count <= 2^32.
+ */
+lcp_status lcp_philox_fill(uint64_t seed, uint32_t c1, uint64_t offset, int64_t count,
+                           uint32_t* out, lcp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LCP_GB300_H */

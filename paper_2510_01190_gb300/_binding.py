@@ -1,0 +1,245 @@
+"""ctypes binding of ``include/lcp.h``: argument marshalling only.
+
+Every function here checks tensor shapes / dtypes / devices, allocates the
+outputs with torch (device memory is plumbing), and calls the C entry point of
+the same name on the current torch CUDA stream.  All arithmetic runs in the
+CUDA kernels of ``liblcp_gb300.so``.  If that library cannot be loaded the call
+raises; nothing falls back to the CPU.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+__all__ = [
+    "LcpError",
+    "load",
+    "library_path",
+    "lcp_stats",
+    "lcp_divergence",
+    "lcp_map",
+    "lcp_fused",
+    "lcp_mc",
+    "lcp_philox_fill",
+    "mask_words_per_row",
+    "unpack_mask",
+    "LCP_F32",
+    "LCP_BF16",
+    "LCP_F16",
+    "LCP_MC_GAUSS",
+    "LCP_MC_EMPIRICAL",
+]
+
+LCP_F32, LCP_BF16, LCP_F16, LCP_F64 = 0, 1, 2, 3
+LCP_MC_GAUSS, LCP_MC_EMPIRICAL = 0, 1
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+_LOCK = threading.Lock()
+
+c_int, c_i64, c_u64, c_u32, c_double = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double
+c_vp, c_fp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)
+
+_SIGNATURES = {
+    "lcp_status_string": (ctypes.c_char_p, [c_int]),
+    "lcp_last_error": (ctypes.c_char_p, []),
+    "lcp_version": (c_int, []),
+    "lcp_stats": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "lcp_divergence": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, c_int, c_double, c_double, c_vp, c_vp, c_vp]),
+    "lcp_map": (c_int, [c_vp, c_vp, c_int, c_int, c_fp, c_int, c_vp, c_int, c_vp, c_vp]),
+    "lcp_fused": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double, c_fp, c_int,
+                          c_vp, c_int, c_vp, c_vp]),
+    "lcp_mc": (c_int, [c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_int, c_int, c_i64, c_int, c_int, c_double,
+                       c_double, c_fp, c_int, c_i64, c_u64, c_u64, c_vp, c_vp, c_vp]),
+    "lcp_philox_fill": (c_int, [c_u64, c_u32, c_u64, c_i64, c_vp, c_vp]),
+}
+
+
+class LcpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+def library_path() -> str:
+    return os.path.join(_PKG, "_lib", "liblcp_gb300.so")
+
+
+def load(build_if_stale: bool = True):
+    """Load (building first if missing or older than its sources) the CUDA library."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        from . import build as _build
+
+        if build_if_stale and _build.is_stale():
+            _build.build()
+        path = library_path()
+        if not os.path.exists(path):
+            raise LcpError(-2, f"CUDA library missing: {path} (run paper_2510_01190_gb300.build.build())")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def _check(status: int):
+    if status != 0:
+        lib = load()
+        msg = lib.lcp_last_error().decode() or lib.lcp_status_string(status).decode()
+        raise LcpError(status, msg)
+
+
+def _stream():
+    return c_vp(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else c_vp(t.data_ptr())
+
+
+def _dtype_code(dt) -> int:
+    if dt == torch.float32:
+        return LCP_F32
+    if dt == torch.bfloat16:
+        return LCP_BF16
+    if dt == torch.float16:
+        return LCP_F16
+    raise ValueError(f"unsupported dtype {dt}")
+
+
+def _members(u, v):
+    if u.dim() != 3 or u.shape != v.shape or u.dtype != v.dtype:
+        raise ValueError("u and v must be [M, H, W] tensors of one shape and dtype")
+    if not (u.is_cuda and v.is_cuda):
+        raise ValueError("members must be CUDA tensors")
+    m, h, w = u.shape
+    for t in (u, v):
+        if t.stride(2) != 1 or t.stride(1) != w:
+            raise ValueError("each member plane must be row-major contiguous [H][W]")
+    if u.stride(0) != v.stride(0):
+        raise ValueError("u and v must share one member stride")
+    return m, h, w, u.stride(0) if m > 1 else h * w
+
+
+def _iso(isovalues):
+    iso = torch.as_tensor(isovalues, dtype=torch.float32).reshape(-1).contiguous().cpu()
+    return iso, iso.numel(), ctypes.cast(iso.data_ptr(), c_fp)
+
+
+def mask_words_per_row(w: int) -> int:
+    return (w - 1 + 31) // 32
+
+
+def _plane(t, h, w, name):
+    if t.dtype != torch.float32 or not t.is_cuda or t.shape != (h, w) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor [{h}, {w}]")
+
+
+def lcp_stats(u, v, ddof: int = 1):
+    """Per-vertex (mean, variance) of u and v over the members (Sec. 3.1)."""
+    m, h, w, stride = _members(u, v)
+    outs = [torch.empty((h, w), dtype=torch.float32, device=u.device) for _ in range(4)]
+    lib = load()
+    _check(lib.lcp_stats(_ptr(u), _ptr(v), _dtype_code(u.dtype), m, h, w, stride, ddof, *map(_ptr, outs), _stream()))
+    return tuple(outs)
+
+
+def lcp_divergence(mu_u, var_u, mu_v, var_v, dx: float = 1.0, dy: float = 1.0):
+    """Divergence Gaussian (Eqs. 2, 3) at every vertex: returns (mu_d, var_d)."""
+    h, w = mu_u.shape
+    for t, n in ((mu_u, "mu_u"), (var_u, "var_u"), (mu_v, "mu_v"), (var_v, "var_v")):
+        _plane(t, h, w, n)
+    mu_d = torch.empty_like(mu_u)
+    var_d = torch.empty_like(mu_u)
+    lib = load()
+    _check(lib.lcp_divergence(_ptr(mu_u), _ptr(var_u), _ptr(mu_v), _ptr(var_v), h, w, float(dx), float(dy),
+                              _ptr(mu_d), _ptr(var_d), _stream()))
+    return mu_d, var_d
+
+
+def _outputs(k, h, w, device, out_dtype, mask, out, mask_out):
+    if out is None:
+        out = torch.empty((k, h - 1, w - 1), dtype=out_dtype, device=device)
+    if mask and mask_out is None:
+        mask_out = torch.empty((k, h - 1, mask_words_per_row(w)), dtype=torch.int32, device=device)
+    return out, (mask_out if mask else None)
+
+
+def lcp_map(mu_d, var_d, isovalues, out_dtype=torch.float32, mask: bool = False, out=None, mask_out=None):
+    """LCP of every cell and isovalue from the divergence Gaussians: returns (lcp, mask_words|None)."""
+    h, w = mu_d.shape
+    _plane(mu_d, h, w, "mu_d")
+    _plane(var_d, h, w, "var_d")
+    iso, k, iso_p = _iso(isovalues)
+    out, mask_out = _outputs(k, h, w, mu_d.device, out_dtype, mask, out, mask_out)
+    lib = load()
+    _check(lib.lcp_map(_ptr(mu_d), _ptr(var_d), h, w, iso_p, k, _ptr(out), _dtype_code(out.dtype),
+                       _ptr(mask_out), _stream()))
+    return out, mask_out
+
+
+def lcp_fused(u, v, isovalues, dx: float = 1.0, dy: float = 1.0, ddof: int = 1, out_dtype=torch.float32,
+              mask: bool = False, out=None, mask_out=None):
+    """Members -> LCP map in one pass (stats, Eqs. 2/3 and LCP fused): returns (lcp, mask_words|None)."""
+    m, h, w, stride = _members(u, v)
+    iso, k, iso_p = _iso(isovalues)
+    out, mask_out = _outputs(k, h, w, u.device, out_dtype, mask, out, mask_out)
+    lib = load()
+    _check(lib.lcp_fused(_ptr(u), _ptr(v), _dtype_code(u.dtype), m, h, w, stride, ddof, float(dx), float(dy),
+                         iso_p, k, _ptr(out), _dtype_code(out.dtype), _ptr(mask_out), _stream()))
+    return out, mask_out
+
+
+def lcp_mc(isovalues, n_samples: int, seed: int, dx: float = 1.0, dy: float = 1.0, mode: str = "gauss",
+           stats=None, members=None, offset: int = 0, estimate: bool = True, counts=None):
+    """Monte Carlo LCP (Sec. 3.2, Sec. 4): returns (estimate|None, counts uint32-as-int32)."""
+    iso, k, iso_p = _iso(isovalues)
+    if mode == "gauss":
+        mu_u, var_u, mu_v, var_v = stats
+        h, w = mu_u.shape
+        for t, n in ((mu_u, "mu_u"), (var_u, "var_u"), (mu_v, "mu_v"), (var_v, "var_v")):
+            _plane(t, h, w, n)
+        dev = mu_u.device
+        args = (LCP_MC_GAUSS, _ptr(mu_u), _ptr(var_u), _ptr(mu_v), _ptr(var_v), None, None, LCP_F32, 0, 0)
+    elif mode == "empirical":
+        u, v = members
+        m, h, w, stride = _members(u, v)
+        dev = u.device
+        args = (LCP_MC_EMPIRICAL, None, None, None, None, _ptr(u), _ptr(v), _dtype_code(u.dtype), m, stride)
+    else:
+        raise ValueError(mode)
+    if counts is None:
+        counts = torch.empty((k, h - 1, w - 1), dtype=torch.int32, device=dev)
+    est = torch.empty((k, h - 1, w - 1), dtype=torch.float32, device=dev) if estimate else None
+    lib = load()
+    _check(lib.lcp_mc(*args, h, w, float(dx), float(dy), iso_p, k, int(n_samples), int(seed) & (2**64 - 1),
+                      int(offset) & (2**64 - 1), _ptr(counts), _ptr(est), _stream()))
+    return est, counts
+
+
+def lcp_philox_fill(seed: int, c1: int, offset: int, count: int, device="cuda"):
+    """Raw Philox-4x32-10 words of the Monte Carlo generator: uint32-as-int32 [count, 4]."""
+    out = torch.empty((count, 4), dtype=torch.int32, device=device)
+    lib = load()
+    _check(lib.lcp_philox_fill(int(seed) & (2**64 - 1), int(c1) & 0xFFFFFFFF, int(offset) & (2**64 - 1), int(count),
+                               _ptr(out), _stream()))
+    return out
+
+
+def unpack_mask(mask_words, w: int):
+    """Expand mask words [K, H-1, ceil((W-1)/32)] to bool [K, H-1, W-1] (bit i % 32 of word i / 32)."""
+    words = mask_words.to(torch.int64) & 0xFFFFFFFF
+    shifts = torch.arange(32, device=words.device, dtype=torch.int64)
+    bits = (words[..., None] >> shifts) & 1
+    return bits.reshape(*words.shape[:-1], -1)[..., : w - 1].to(torch.bool)
