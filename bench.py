@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused closed-form LCP path on the lat-lon-shaped workload.
+
+Workload: 721 x 1440 grid (0.25 degree lat-lon), 51 members of (u, v) in fp32,
+8 isovalues, dx = dy = 1 (synthetic Fourier-mode ensemble; the paper's wind and
+Red Sea data are not available).  One step = one ``lcp_fused`` call: member
+statistics, divergence Gaussian, LCP of every cell and isovalue, and the
+mean-field crossing mask, from member bytes resident in HBM.
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank processes its own
+field (weak scaling, no data-path collective); timing is the max over ranks.
+
+``--impl reference`` times the FP64 CPU oracle (the reference of this build)
+on the same workload, a bounded row band per step, on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LCP cells/sec & % HBM peak; vs GPU MC at equal 1e-3 max abs LCP error"
+UNIT = "cells/s"
+H, W, M, K = 721, 1440, 51, 8
+WORKLOAD = "latlon 721x1440, 51 members fp32 (u,v), 8 isovalues; fused closed-form LCP + mean-field mask"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--no-mc", action="store_true", help="skip the Monte Carlo equal-error comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0: float, t1: float):
+        inside = [p for (t, p) in self.samples if t0 <= t <= t1]
+        used = inside
+        if not used and self.samples:  # timed region shorter than the sampling period: nearest samples
+            mid = 0.5 * (t0 + t1)
+            used = [min(self.samples, key=lambda s: abs(s[0] - mid))[1]]
+        if not used:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(p[1]) for p in used if num(p[1]) is not None]
+        smax = [num(p[2]) for p in used if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in used for i in range(4) if p[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(inside), "power_w_max": max((num(p[3]) or 0) for p in used)}
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    valid only while fused.cu is byte-identical to the source that was profiled."""
+    src = os.path.join(ROOT, "paper_2510_01190_gb300", "csrc", "fused.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        txt = open(os.path.join(ROOT, "profiles", "lcp_fused_latlon_721x1440_m51_k8.md")).read()
+    except OSError:
+        return None
+    m_t = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", txt)
+    m_s = re.search(r"fused_cu_sha256:\s*([0-9a-f]{64})", txt)
+    if not m_t or not m_s or m_s.group(1) != sha:
+        return None
+    return int(m_t.group(1))
+
+
+# ---------------------------------------------------------------------------
+def make_workload():
+    from paper_2510_01190_gb300 import synth
+
+    return synth.fourier_ensemble(0, h=H, w=W, m=M, k=K)
+
+
+def cpu_baseline(d, budget_s=12.0, rows=None):
+    """Time the FP64 oracle, as it stands, on row bands of the workload."""
+    import oracle as O
+
+    iso = d["isovalues"]
+    rows = rows or 61
+    cells = 0
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        j0 = (n * 97) % (H - rows)
+        O.lcp_closed_form(d["u"][:, j0:j0 + rows], d["v"][:, j0:j0 + rows], 1.0, 1.0, iso)
+        cells += (rows - 1) * (W - 1)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} bands of {rows} rows x {W} cols x {M} members, K={K} (FP64 numpy, single thread)",
+            "seconds": round(dt, 2)}
+
+
+def reference_arm(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    d = make_workload()
+    # size each step so that warmup + steps fit in ~90 s of CPU work
+    t0 = time.perf_counter()
+    import oracle as O
+
+    O.lcp_closed_form(d["u"][:, :9], d["v"][:, :9], 1.0, 1.0, d["isovalues"])
+    per_row = max((time.perf_counter() - t0) / 9, 1e-4)
+    total_steps = args.steps + args.warmup
+    rows = int(max(3, min(H - 1, 90.0 / (total_steps * per_row))))
+    for _ in range(args.warmup):
+        O.lcp_closed_form(d["u"][:, :rows], d["v"][:, :rows], 1.0, 1.0, d["isovalues"])
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        j0 = (s * 97) % (H - rows)
+        O.lcp_closed_form(d["u"][:, j0:j0 + rows], d["v"][:, j0:j0 + rows], 1.0, 1.0, d["isovalues"])
+    dt = time.perf_counter() - t0
+    cells = args.steps * (rows - 1) * (W - 1)
+    value = cells / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "M": M, "K": K,
+                   "sample": f"row band of {rows} rows per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": f"{args.steps} bands of {rows} rows x {W} cols x {M} members"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def mc_equal_error(lib, torch, u, v, iso, t_closed_s):
+    """GPU Monte Carlo (Gaussian mode, same fitted statistics) against the
+    closed form on interior cells: fit max-abs error = c / sqrt(S), solve for
+    the S reaching 1e-3 and 1e-2, and extrapolate its time (linear in S)."""
+    st = lib.lcp_stats(u, v, 1)
+    closed, _ = lib.lcp_fused(u, v, iso)
+    ref = closed[:, 1:-1, 1:-1].double()
+    rows = []
+    for s in (256, 1024, 4096):
+        lib.lcp_mc(iso, s, seed=11, stats=st)  # warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        est, _ = lib.lcp_mc(iso, s, seed=1234 + s, stats=st)
+        e1.record()
+        torch.cuda.synchronize()
+        err = (est[:, 1:-1, 1:-1].double() - ref).abs()
+        rows.append((s, e0.elapsed_time(e1) / 1e3, err.max().item(), err.pow(2).sum().item()))
+    cs = [e * np.sqrt(s) for (s, _, e, _) in rows]
+    c = float(np.median(cs))
+    rate = float(np.median([t / s for (s, t, _, _) in rows]))  # seconds per sample
+    out = {"samples": [r[0] for r in rows], "ms": [round(1e3 * r[1], 3) for r in rows],
+           "max_abs_err": [round(r[2], 5) for r in rows], "sse": [round(r[3], 3) for r in rows],
+           "err_sqrtS": round(c, 4), "interior_cells_only": True}
+    for tol, key in ((1e-3, "1e-3"), (1e-2, "1e-2")):
+        s_star = (c / tol) ** 2
+        out[f"S_star_{key}"] = round(s_star)
+        out[f"t_mc_s_{key}"] = round(s_star * rate, 4)
+        out[f"speedup_closed_vs_mc_{key}"] = round(s_star * rate / t_closed_s, 1)
+    return out
+
+
+def our_arm(args):
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = False
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = True
+    import paper_2510_01190_gb300 as lib
+
+    lib.load()
+    d = make_workload()
+    iso = d["isovalues"]
+    u = torch.from_numpy(d["u"]).to(dev)
+    v = torch.from_numpy(d["v"]).to(dev)
+    Hc, Wc = H - 1, W - 1
+    out = torch.empty((K, Hc, Wc), dtype=torch.float32, device=dev)
+    mask = torch.empty((K, Hc, lib.mask_words_per_row(W)), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        lib.lcp_fused(u, v, iso, 1.0, 1.0, 1, mask=True, out=out, mask_out=mask)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local).start()
+    time.sleep(0.35)  # let the sampler start
+    n = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    if pg:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    for i in range(n):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if pg:
+        torch.distributed.barrier()
+    time.sleep(0.25)
+    clocks.stop()
+    total_ms = ev[0][0].elapsed_time(ev[-1][1])
+    kern_ms = sum(a.elapsed_time(b) for a, b in ev) / n
+    if pg:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+    ms_per_step = total_ms / n
+    value = world * Hc * Wc / (ms_per_step / 1e3)
+
+    # algorithmic bytes of one launch: members read once + LCP map + mask written once
+    n_words = lib.mask_words_per_row(W)
+    alg_bytes = 2 * M * H * W * 4 + K * Hc * Wc * 4 + K * Hc * n_words * 4
+    peak, peak_kind = measured_hbm_peak()
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": profiled_traffic(), "peak_kind": peak_kind,
+            "kernel": "lcp_fused (fused_kernel<float,4,float,MS>)", "alg_bytes_per_launch": alg_bytes,
+            "kernel_ms": round(kern_ms, 5)}
+
+    # end to end through the host-buffer API: pinned members in, LCP + mask out
+    e2e = None
+    if args.e2e_steps > 0:
+        uh = torch.from_numpy(d["u"]).pin_memory()
+        vh = torch.from_numpy(d["v"]).pin_memory()
+        oh = torch.empty((K, Hc, Wc), dtype=torch.float32).pin_memory()
+        mh = torch.empty((K, Hc, n_words), dtype=torch.int32).pin_memory()
+        for _ in range(3):
+            lib.lcp_fused_host(uh, vh, iso, out_host=oh, mask_host=mh, device=dev)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            lib.lcp_fused_host(uh, vh, iso, out_host=oh, mask_host=mh, device=dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1) / args.e2e_steps
+        e2e = {"value": world * Hc * Wc / (e_ms / 1e3), "unit": UNIT, "ms_per_step": round(e_ms, 4),
+               "h2d_bytes_per_step": 2 * M * H * W * 4, "d2h_bytes_per_step": K * Hc * Wc * 4 + K * Hc * n_words * 4}
+
+    vs_mc = None
+    if not args.no_mc and rank == 0:
+        vs_mc = mc_equal_error(lib, torch, u, v, iso, kern_ms / 1e3)
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        cpu = cpu_baseline(d)
+
+    if rank == 0:
+        clk = clocks.summary(t_wall0, t_wall1)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "H": H, "W": W, "M": M, "K": K, "global_batch": world,
+                       "parallelism": f"independent fields x{world}" if world > 1 else "single",
+                       "l2": "no flush: inputs 424 MB > 129 MB L2",
+                       "lcp_values_per_s": value * K, "hbm_frac_of_measured": roof["frac"]},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "vs_mc": vs_mc,
+            "clocks": clk, "gpu_launches": n,
+            "gpu": torch.cuda.get_device_name(dev),
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -23,6 +23,7 @@ __all__ = [
     "lcp_divergence",
     "lcp_map",
     "lcp_fused",
+    "lcp_fused_host",
     "lcp_mc",
     "lcp_philox_fill",
     "mask_words_per_row",
@@ -199,6 +200,47 @@ def lcp_fused(u, v, isovalues, dx: float = 1.0, dy: float = 1.0, ddof: int = 1, 
     _check(lib.lcp_fused(_ptr(u), _ptr(v), _dtype_code(u.dtype), m, h, w, stride, ddof, float(dx), float(dy),
                          iso_p, k, _ptr(out), _dtype_code(out.dtype), _ptr(mask_out), _stream()))
     return out, mask_out
+
+
+class _HostStaging:
+    """Device buffers reused by ``lcp_fused_host`` across calls of one shape."""
+
+    def __init__(self):
+        self.key = None
+        self.bufs = None
+
+
+_STAGING = _HostStaging()
+
+
+def lcp_fused_host(u_host, v_host, isovalues, dx: float = 1.0, dy: float = 1.0, ddof: int = 1,
+                   out_host=None, mask_host=None, device="cuda"):
+    """End-to-end call for host-resident ensembles: copy the members (pinned
+    host tensors [M, H, W]) to the device, run ``lcp_fused`` and copy the LCP
+    map (and mask words, if ``mask_host`` is given) back into the pinned host
+    outputs, all on the current stream.  Returns (out_host, mask_host); the
+    copies are complete once the stream is synchronised."""
+    if u_host.is_cuda or v_host.is_cuda:
+        raise ValueError("lcp_fused_host takes host tensors")
+    m, h, w = u_host.shape
+    iso, k, _ = _iso(isovalues)
+    key = (tuple(u_host.shape), u_host.dtype, k, mask_host is not None, str(device))
+    if _STAGING.key != key:
+        _STAGING.bufs = (torch.empty_like(u_host, device=device), torch.empty_like(v_host, device=device),
+                         torch.empty((k, h - 1, w - 1), dtype=torch.float32, device=device),
+                         torch.empty((k, h - 1, mask_words_per_row(w)), dtype=torch.int32, device=device)
+                         if mask_host is not None else None)
+        _STAGING.key = key
+    ud, vd, od, md = _STAGING.bufs
+    ud.copy_(u_host, non_blocking=True)
+    vd.copy_(v_host, non_blocking=True)
+    lcp_fused(ud, vd, iso, dx, dy, ddof, mask=md is not None, out=od, mask_out=md)
+    if out_host is None:
+        out_host = torch.empty(od.shape, dtype=od.dtype, pin_memory=True)
+    out_host.copy_(od, non_blocking=True)
+    if mask_host is not None:
+        mask_host.copy_(md, non_blocking=True)
+    return out_host, mask_host
 
 
 def lcp_mc(isovalues, n_samples: int, seed: int, dx: float = 1.0, dy: float = 1.0, mode: str = "gauss",

@@ -1,0 +1,204 @@
+// Internal helpers shared by the kernels of liblcp_gb300 (sm_103a).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lcp.h"
+
+namespace lcp {
+
+// ---------------------------------------------------------------------------
+// Host-side error plumbing (thread-local message behind lcp_last_error)
+// ---------------------------------------------------------------------------
+lcp_status fail(lcp_status s, const char* fmt, ...);
+lcp_status check_launch(const char* what);  // cudaGetLastError after a launch
+int num_sms();                              // SM count of the current device (cached per device)
+bool aligned16(const void* p);
+
+// Isovalues travel by value in the launch parameters (no device copy, safe to
+// capture in a CUDA graph).  Kernels take them as __grid_constant__ so that a
+// runtime index reads parameter space directly.
+constexpr int kMaxIsoPerLaunch = 64;
+struct IsoParams {
+    int K;  // isovalues in this launch
+    float c[kMaxIsoPerLaunch];
+};
+
+// ---------------------------------------------------------------------------
+// Element loads: VEC consecutive elements of one member row as floats
+// ---------------------------------------------------------------------------
+template <typename T, int VEC>
+struct Loader;
+
+template <>
+struct Loader<float, 1> {
+    using raw_t = float;
+    static __device__ __forceinline__ raw_t load(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ void cvt(const raw_t& r, float* x) { x[0] = r; }
+};
+
+template <>
+struct Loader<float, 4> {
+    using raw_t = float4;
+    static __device__ __forceinline__ raw_t load(const float* p) {
+        float4 r;
+        asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                     : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                     : "l"(p));
+        return r;
+    }
+    static __device__ __forceinline__ void cvt(const raw_t& r, float* x) {
+        x[0] = r.x; x[1] = r.y; x[2] = r.z; x[3] = r.w;
+    }
+};
+
+template <>
+struct Loader<__nv_bfloat16, 1> {
+    using raw_t = unsigned short;
+    static __device__ __forceinline__ raw_t load(const __nv_bfloat16* p) {
+        return __ldg(reinterpret_cast<const unsigned short*>(p));
+    }
+    static __device__ __forceinline__ void cvt(const raw_t& r, float* x) {
+        x[0] = __uint_as_float(static_cast<uint32_t>(r) << 16);
+    }
+};
+
+template <>
+struct Loader<__nv_bfloat16, 8> {
+    using raw_t = uint4;
+    static __device__ __forceinline__ raw_t load(const __nv_bfloat16* p) {
+        uint4 r;
+        asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                     : "l"(p));
+        return r;
+    }
+    static __device__ __forceinline__ void cvt(const raw_t& r, float* x) {
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            x[2 * i] = __uint_as_float(w[i] << 16);          // low half = lower address
+            x[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+        }
+    }
+};
+
+template <typename OutT>
+__device__ __forceinline__ OutT to_out(float x);
+template <>
+__device__ __forceinline__ float to_out<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __half to_out<__half>(float x) { return __float2half_rn(x); }
+
+// ---------------------------------------------------------------------------
+// P(D < c) and P(D >= c) for D ~ N(mu, var), complementary erfc form
+// ---------------------------------------------------------------------------
+// t = (mu - c) / (sigma sqrt 2); p = erfc(t)/2, q = erfc(-t)/2 = 1 - p.  Only
+// erfc(|t|) <= 1 is evaluated: the small one of (p, q) is that tail value
+// itself (full relative accuracy) and the large one is 1 minus it, which has
+// no cancellation because it lies in [1/2, 1].  var == 0 gives the indicator;
+// a NaN mean or variance gives NaN for both.
+__device__ __forceinline__ void below_above(float mu, float var, float c, float& p, float& q) {
+    if (var == 0.0f) {
+        p = (mu < c) ? 1.0f : 0.0f;
+        q = 1.0f - p;
+        return;
+    }
+    const float t = (mu - c) * rsqrtf(2.0f * var);
+    const float e = 0.5f * erfcf(fabsf(t));
+    if (t >= 0.0f) {
+        p = e;
+        q = 1.0f - e;
+    } else {
+        q = e;
+        p = 1.0f - e;
+    }
+}
+
+// Clamp to [0, 1] without turning NaN into a number.
+__device__ __forceinline__ float clamp01(float x) {
+    if (x < 0.0f) x = 0.0f;
+    if (x > 1.0f) x = 1.0f;
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint2 k) {
+    constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;  // round multipliers
+    constexpr uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;  // Weyl key increments
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(kM0, x.x), lo0 = kM0 * x.x;
+        const uint32_t hi1 = __umulhi(kM1, x.z), lo1 = kM1 * x.z;
+        x = make_uint4(hi1 ^ x.y ^ k.x, lo1, hi0 ^ x.w ^ k.y, lo0);
+        k.x += kW0;
+        k.y += kW1;
+    }
+    return x;
+}
+
+// Uniform in (0, 1): midpoint of the 2^-24 sub-interval indexed by the top 24 bits.
+__device__ __forceinline__ float uniform01(uint32_t w) {
+    return (__uint2float_rn(w >> 8) + 0.5f) * 5.9604644775390625e-8f;
+}
+
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
+    const float r = sqrtf(-2.0f * logf(uniform01(a)));
+    float s, c;
+    sincospif(2.0f * uniform01(b), &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+}  // namespace lcp
+
+namespace lcp {
+
+// Argument checks shared by the entry points that read member planes.
+inline lcp_status check_members(const char* fn, const void* u, const void* v, lcp_dtype dt, int M, int H, int W,
+                                int64_t stride, int ddof) {
+    if (!u || !v) return fail(LCP_ERR_ARG, "%s: u and v must be non-NULL device pointers", fn);
+    if (dt != LCP_F32 && dt != LCP_BF16) return fail(LCP_ERR_ARG, "%s: member dtype must be LCP_F32 or LCP_BF16", fn);
+    if (H < 2 || W < 2) return fail(LCP_ERR_ARG, "%s: need H >= 2 and W >= 2 (got %d x %d)", fn, H, W);
+    if (M < 1) return fail(LCP_ERR_ARG, "%s: need M >= 1 (got %d)", fn, M);
+    if (ddof != 0 && ddof != 1) return fail(LCP_ERR_ARG, "%s: ddof must be 0 or 1", fn);
+    if (M - ddof < 1) return fail(LCP_ERR_ARG, "%s: need M - ddof >= 1", fn);
+    if (M > 1 && stride < (int64_t)H * W) return fail(LCP_ERR_ARG, "%s: member_stride < H*W", fn);
+    const size_t esz = dt == LCP_F32 ? 4 : 2;
+    if (((uintptr_t)u | (uintptr_t)v) % esz) return fail(LCP_ERR_ARG, "%s: member pointers misaligned", fn);
+    return LCP_OK;
+}
+
+inline lcp_status check_iso(const char* fn, const float* iso, int K) {
+    if (!iso) return fail(LCP_ERR_ARG, "%s: iso must be a non-NULL host array", fn);
+    if (K < 1 || K > LCP_MAX_ISOVALUES) return fail(LCP_ERR_ARG, "%s: need 1 <= K <= %d", fn, LCP_MAX_ISOVALUES);
+    return LCP_OK;
+}
+
+inline lcp_status check_spacing(const char* fn, double dx, double dy) {
+    if (!(dx > 0.0) || !(dy > 0.0) || dx > 1e30 || dy > 1e30)
+        return fail(LCP_ERR_ARG, "%s: dx and dy must be finite and > 0", fn);
+    return LCP_OK;
+}
+
+// Stencil scale factors 1/(2 dx), 1/dx (first/last column) and their squares,
+// rounded once from double.
+struct Spacing {
+    float sx2, sx1, sy2, sy1;      // 1/(2dx), 1/dx, 1/(2dy), 1/dy
+    float sx2q, sx1q, sy2q, sy1q;  // squares
+};
+inline Spacing make_spacing(double dx, double dy) {
+    Spacing s;
+    s.sx2 = (float)(0.5 / dx); s.sx1 = (float)(1.0 / dx);
+    s.sy2 = (float)(0.5 / dy); s.sy1 = (float)(1.0 / dy);
+    s.sx2q = (float)(0.25 / (dx * dx)); s.sx1q = (float)(1.0 / (dx * dx));
+    s.sy2q = (float)(0.25 / (dy * dy)); s.sy1q = (float)(1.0 / (dy * dy));
+    return s;
+}
+
+}  // namespace lcp

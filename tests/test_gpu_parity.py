@@ -1,0 +1,269 @@
+"""GPU parity: every C-ABI entry point against the FP64 oracle on the same inputs.
+
+Tolerances (stated here, derived in the design doc):
+* LCP in fp32: max |gpu - oracle| <= 1e-5 (the target), observed ~1e-6.
+* LCP in fp16: |gpu - fp16(oracle)| <= 1 fp16 ulp of the value.
+* Mean-field masks: bit-exact on dyadic data (exact arithmetic on both sides);
+  on general data bit-exact outside a guard band |mu_d - c| <= 1e-5 (|mu_d| + 1).
+* Statistics / divergence: FP32 rounding bounds (relative 2e-6 / 2e-5).
+* Monte Carlo: same Philox streams on both sides, so crossing counts agree
+  except where a divergence sample lies within FP32 rounding of c.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2510_01190_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+LCP_TOL = 1e-5
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def _np(t):
+    return t.detach().float().cpu().numpy().astype(np.float64)
+
+
+def _fields(h, w, m, seed, kind="fourier", k=4):
+    if kind == "fourier":
+        d = synth.fourier_ensemble(seed, h=h, w=w, m=m, k=k)
+    elif kind == "sources":
+        d = synth.point_sources_ensemble(seed, h=h, w=w, m=m)
+    else:
+        raise ValueError(kind)
+    return d
+
+
+def _oracle_mask_guard(mu_d, iso):
+    """cells whose vertices are all clear of the FP32 rounding band around c"""
+    out = []
+    for c in iso:
+        clear = np.abs(mu_d - c) > 1e-5 * (np.abs(mu_d) + 1.0)
+        out.append(clear[:-1, :-1] & clear[:-1, 1:] & clear[1:, :-1] & clear[1:, 1:])
+    return np.stack(out)
+
+
+# ---------------------------------------------------------------------------
+# statistics, divergence, map (unfused path)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("h,w,m,ddof", [(64, 64, 20, 1), (37, 53, 7, 0), (5, 3, 1, 0), (2, 2, 2, 1), (181, 360, 51, 1)])
+def test_stats_parity(lib, h, w, m, ddof):
+    d = _fields(h, w, m, seed=h * 7 + w)
+    mu_u, var_u, mu_v, var_v = lib.lcp_stats(_dev(d["u"]), _dev(d["v"]), ddof)
+    for x, mu, var in ((d["u"], mu_u, var_u), (d["v"], mu_v, var_v)):
+        om, ov = O.ensemble_stats(x, ddof)
+        scale = np.abs(om) + np.sqrt(ov) + 1e-30
+        assert np.max(np.abs(_np(mu) - om) / scale) < 2e-6
+        assert np.max(np.abs(_np(var) - ov) / (ov + 1e-12)) < 2e-5
+
+
+def test_stats_bf16_and_strided_members(lib):
+    d = _fields(40, 72, 12, seed=3)
+    u16 = _dev(d["u"], torch.bfloat16)
+    v16 = _dev(d["v"], torch.bfloat16)
+    # members embedded in a larger buffer: member stride > H*W
+    big_u = torch.zeros((12, 40 * 72 + 64), device="cuda", dtype=torch.bfloat16)
+    big_v = torch.zeros_like(big_u)
+    big_u[:, : 40 * 72] = u16.reshape(12, -1)
+    big_v[:, : 40 * 72] = v16.reshape(12, -1)
+    su = big_u.as_strided((12, 40, 72), (40 * 72 + 64, 72, 1))
+    sv = big_v.as_strided((12, 40, 72), (40 * 72 + 64, 72, 1))
+    for uu, vv in ((u16, v16), (su, sv)):
+        mu_u, var_u, mu_v, var_v = lib.lcp_stats(uu, vv, 1)
+        om, ov = O.ensemble_stats(_np(u16), 1)
+        assert np.max(np.abs(_np(mu_u) - om) / (np.abs(om) + np.sqrt(ov))) < 2e-6
+        assert np.max(np.abs(_np(var_u) - ov) / (ov + 1e-12)) < 2e-5
+
+
+@pytest.mark.parametrize("h,w,dx,dy", [(64, 64, 1.0, 1.0), (9, 130, 0.5, 2.0), (2, 2, 1.0, 3.0), (300, 7, 0.1, 0.1)])
+def test_divergence_parity(lib, h, w, dx, dy):
+    st = synth.random_stats(h * w, h, w, zero_fraction=0.05)
+    mu_d, var_d = lib.lcp_divergence(*map(_dev, st), dx, dy)
+    om, ov = O.divergence_gaussian(*[s.astype(np.float64) for s in st], dx, dy)
+    scale = np.abs(om) + np.sqrt(ov) + 1e-30
+    assert np.max(np.abs(_np(mu_d) - om) / scale) < 2e-6
+    assert np.max(np.abs(_np(var_d) - ov) / (ov + 1e-30)) < 2e-6
+
+
+@pytest.mark.parametrize("h,w,k", [(64, 64, 1), (33, 517, 5), (2, 2, 3), (130, 33, 70)])
+def test_map_parity(lib, h, w, k):
+    st = synth.random_stats(7 + h, h, w, zero_fraction=0.1)
+    om, ov = O.divergence_gaussian(*[s.astype(np.float64) for s in st], 1.0, 1.0)
+    mu32, var32 = om.astype(np.float32), ov.astype(np.float32)
+    var32[::5, ::3] = 0.0
+    iso = np.quantile(mu32, np.linspace(0.1, 0.9, k)).astype(np.float32)
+    lcp, mask = lib.lcp_map(_dev(mu32), _dev(var32), iso, mask=True)
+    ref = O.level_crossing_probability(mu32, var32, iso)
+    assert np.max(np.abs(_np(lcp) - ref)) <= LCP_TOL
+    got_mask = lib.unpack_mask(mask, w).cpu().numpy()
+    want_mask = O.mean_field_crossing(mu32, iso)
+    assert np.array_equal(got_mask, want_mask)  # exact: same fp32 mu_d on both sides
+
+
+# ---------------------------------------------------------------------------
+# fused path
+# ---------------------------------------------------------------------------
+FUSED_CASES = [
+    # h, w, m, k, generator      (vector path needs W % 4 == 0; others take the scalar path)
+    (64, 64, 20, 1, "sources"),
+    (181, 360, 51, 8, "fourier"),
+    (2, 2, 1, 1, "fourier"),
+    (3, 5, 2, 2, "fourier"),
+    (45, 1028, 9, 3, "fourier"),   # 3 column tiles, ragged last tile
+    (70, 1031, 6, 2, "fourier"),   # odd W: scalar loads, 9 column tiles
+    (97, 64, 40, 33, "fourier"),   # K > 32: two isovalue passes
+    (300, 16, 3, 4, "fourier"),    # tall and narrow: many bands
+]
+
+
+@pytest.mark.parametrize("h,w,m,k,kind", FUSED_CASES)
+def test_fused_parity(lib, h, w, m, k, kind):
+    d = _fields(h, w, m, seed=h + 3 * w, kind=kind, k=k) if kind == "fourier" else _fields(h, w, m, 0, kind)
+    iso = d["isovalues"][:k] if len(d["isovalues"]) >= k else np.linspace(-0.5, 0.5, k).astype(np.float32)
+    ddof = 1 if m > 1 else 0
+    lcp, mask = lib.lcp_fused(_dev(d["u"]), _dev(d["v"]), iso, d["dx"], d["dy"], ddof=ddof, mask=True)
+    ref = O.lcp_closed_form(d["u"], d["v"], d["dx"], d["dy"], iso, ddof)
+    err = np.abs(_np(lcp) - ref["lcp"])
+    assert np.max(err) <= LCP_TOL, np.max(err)
+    guard = _oracle_mask_guard(ref["mu_d"], iso)
+    got = lib.unpack_mask(mask, w).cpu().numpy()
+    assert np.array_equal(got[guard], ref["mask"][guard])
+
+
+def test_fused_equals_unfused_chain(lib):
+    d = _fields(90, 200, 17, seed=5, k=5)
+    u, v = _dev(d["u"]), _dev(d["v"])
+    iso = d["isovalues"]
+    fused, fm = lib.lcp_fused(u, v, iso, mask=True)
+    st = lib.lcp_stats(u, v, 1)
+    mu_d, var_d = lib.lcp_divergence(*st)
+    chain, cm = lib.lcp_map(mu_d, var_d, iso, mask=True)
+    assert torch.max(torch.abs(fused - chain)).item() <= 2e-6
+
+
+def test_fused_fp16_output_within_one_ulp(lib):
+    d = _fields(61, 256, 10, seed=9, k=4)
+    lcp, _ = lib.lcp_fused(_dev(d["u"]), _dev(d["v"]), d["isovalues"], out_dtype=torch.float16)
+    ref = O.lcp_closed_form(d["u"], d["v"], 1.0, 1.0, d["isovalues"])["lcp"]
+    ref16 = ref.astype(np.float16).astype(np.float64)
+    ulp = np.spacing(np.abs(ref16).astype(np.float16)).astype(np.float64)
+    assert np.all(np.abs(_np(lcp) - ref16) <= ulp + 1e-12)
+
+
+def test_fused_bf16_members(lib):
+    d = _fields(64, 512, 20, seed=11, k=4)
+    u16, v16 = _dev(d["u"], torch.bfloat16), _dev(d["v"], torch.bfloat16)
+    lcp, _ = lib.lcp_fused(u16, v16, d["isovalues"])
+    ref = O.lcp_closed_form(_np(u16), _np(v16), 1.0, 1.0, d["isovalues"])["lcp"]  # same bf16-rounded values
+    assert np.max(np.abs(_np(lcp) - ref)) <= LCP_TOL
+    # odd width: scalar bf16 path
+    d = _fields(33, 99, 5, seed=12, k=2)
+    u16, v16 = _dev(d["u"], torch.bfloat16), _dev(d["v"], torch.bfloat16)
+    lcp, _ = lib.lcp_fused(u16, v16, d["isovalues"])
+    ref = O.lcp_closed_form(_np(u16), _np(v16), 1.0, 1.0, d["isovalues"])["lcp"]
+    assert np.max(np.abs(_np(lcp) - ref)) <= LCP_TOL
+
+
+def test_fused_large_offset_keeps_accuracy(lib):
+    """|mean| / sigma ~ 2e5: the member-0 shift cancels the offset exactly."""
+    d = _fields(48, 128, 20, seed=13, k=3)
+    u = (d["u"] * 0.05 + 1e4).astype(np.float32)
+    v = (d["v"] * 0.05 + 1e4).astype(np.float32)
+    iso = (d["isovalues"] * 0.05).astype(np.float32)
+    lcp, _ = lib.lcp_fused(_dev(u), _dev(v), iso)
+    ref = O.lcp_closed_form(u, v, 1.0, 1.0, iso)["lcp"]
+    assert np.max(np.abs(_np(lcp) - ref)) <= LCP_TOL
+
+
+def test_fused_dyadic_zero_variance_is_bit_exact(lib):
+    for (h, w, dx) in ((33, 68, 1.0), (20, 77, 0.5)):
+        d = synth.dyadic_ensemble(h * w, h, w, m=4, k=3)
+        lcp, mask = lib.lcp_fused(_dev(d["u"]), _dev(d["v"]), d["isovalues"], dx, dx, mask=True)
+        ref = O.lcp_closed_form(d["u"], d["v"], dx, dx, d["isovalues"])
+        assert np.array_equal(lib.unpack_mask(mask, w).cpu().numpy(), ref["mask"])
+        assert np.array_equal(_np(lcp), ref["lcp"])  # var = 0: LCP is the mask exactly
+
+
+def test_fused_nan_member_propagates(lib):
+    d = _fields(20, 40, 6, seed=14, k=2)
+    u = d["u"].copy()
+    u[3, 10, 17] = np.nan
+    lcp, _ = lib.lcp_fused(_dev(u), _dev(d["v"]), d["isovalues"])
+    ref = O.lcp_closed_form(u, d["v"], 1.0, 1.0, d["isovalues"])["lcp"]
+    got = _np(lcp)
+    assert np.array_equal(np.isnan(got), np.isnan(ref)) and np.isnan(ref).any()
+    ok = ~np.isnan(ref)
+    assert np.max(np.abs(got[ok] - ref[ok])) <= LCP_TOL
+
+
+@pytest.mark.slow
+def test_fused_full_size_latlon(lib):
+    """The 721 x 1440 x 51, K = 8 workload in the bench's launch configuration,
+    compared with the oracle on every cell."""
+    d = synth.fourier_ensemble(0)
+    u, v = _dev(d["u"]), _dev(d["v"])
+    lcp, mask = lib.lcp_fused(u, v, d["isovalues"], mask=True)
+    ref = O.lcp_closed_form(d["u"], d["v"], 1.0, 1.0, d["isovalues"])
+    assert np.max(np.abs(_np(lcp) - ref["lcp"])) <= LCP_TOL
+    guard = _oracle_mask_guard(ref["mu_d"], d["isovalues"])
+    assert np.array_equal(lib.unpack_mask(mask, 1440).cpu().numpy()[guard], ref["mask"][guard])
+
+
+# ---------------------------------------------------------------------------
+# Monte Carlo
+# ---------------------------------------------------------------------------
+def test_philox_fill_bit_exact(lib):
+    for seed, c1, off in ((0, 0, 0), (2**40 + 7, 12345, 2**33 + 5), (2**64 - 1, 2**32 - 1, 2**64 - 1)):
+        got = lib.lcp_philox_fill(seed, c1, off, 5000).cpu().numpy().view(np.uint32)
+        ctr = np.zeros((5000, 4), np.uint64)
+        ctr[:, 0] = np.arange(5000)
+        ctr[:, 1] = c1
+        ctr[:, 2] = off & 0xFFFFFFFF
+        ctr[:, 3] = off >> 32
+        want = O.philox4x32_10(ctr, (seed & 0xFFFFFFFF, seed >> 32))
+        assert np.array_equal(got, want)
+
+
+def _count_agreement(got, want, n_samples):
+    diff = np.abs(got.astype(np.int64) - want)
+    assert diff.max() <= 2, diff.max()
+    assert np.mean(diff > 0) < 2e-3
+
+
+@pytest.mark.parametrize("h,w,k,s", [(40, 70, 2, 64), (9, 33, 17, 31), (2, 2, 1, 5)])
+def test_mc_gauss_counts_match_oracle(lib, h, w, k, s):
+    st = synth.random_stats(h + w, h, w, sd_scale=0.4)
+    om, _ = O.divergence_gaussian(*[x.astype(np.float64) for x in st], 1.0, 1.0)
+    iso = np.quantile(om, np.linspace(0.2, 0.8, k)).astype(np.float32)
+    est, counts = lib.lcp_mc(iso, s, seed=77, dx=1.0, dy=1.0, stats=tuple(map(_dev, st)), offset=3)
+    _, want = O.mc_lcp(iso, s, seed=77, dx=1.0, dy=1.0, stats=st, offset=3)
+    got = counts.cpu().numpy().view(np.uint32)
+    _count_agreement(got, want, s)
+    assert np.max(np.abs(_np(est) - got / s)) < 1e-6
+
+
+def test_mc_empirical_counts_match_oracle(lib):
+    d = _fields(30, 44, 9, seed=21, k=3)
+    iso = d["isovalues"]
+    est, counts = lib.lcp_mc(iso, 40, seed=5, mode="empirical", members=(_dev(d["u"]), _dev(d["v"])))
+    _, want = O.mc_lcp(iso, 40, seed=5, dx=1.0, dy=1.0, mode="empirical", members=(d["u"], d["v"]))
+    _count_agreement(counts.cpu().numpy().view(np.uint32), want, 40)
+
+
+def test_mc_converges_to_closed_form(lib):
+    d = synth.point_sources_ensemble(1)
+    u, v = _dev(d["u"]), _dev(d["v"])
+    st = lib.lcp_stats(u, v, 1)
+    iso = np.array([0.0, -0.02], np.float32)
+    closed, _ = lib.lcp_fused(u, v, iso)
+    s = 20000
+    est, _ = lib.lcp_mc(iso, s, seed=1, stats=st)
+    c, e = _np(closed)[:, 1:-1, 1:-1], _np(est)[:, 1:-1, 1:-1]  # interior cells (independent vertices)
+    se = np.sqrt(c * (1 - c) / s) + 1e-9
+    assert np.abs((e - c) / se).max() < 5.5

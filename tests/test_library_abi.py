@@ -1,0 +1,102 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, exports
+every symbol declared in include/lcp.h, and rejects bad arguments on the host
+(before any CUDA call, so these run without a GPU).  Also checks that the
+product package never reaches the oracle."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lcp.h")
+
+FAKE = ctypes.c_void_p(256)  # never dereferenced: validation fails first
+
+
+@pytest.fixture(scope="module")
+def clib():
+    from paper_2510_01190_gb300 import _binding
+
+    try:
+        return _binding.load()
+    except RuntimeError as e:  # no nvcc at all: nothing to check
+        pytest.skip(f"library not buildable here: {e}")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lcp_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_hot_path_entry_points():
+    names = declared_functions()
+    for want in ("lcp_stats", "lcp_divergence", "lcp_map", "lcp_fused", "lcp_mc"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(clib):
+    for name in declared_functions():
+        assert hasattr(clib, name), name
+
+
+def test_status_strings_and_version(clib):
+    for code in (0, -1, -2, -3, -4, -5):
+        assert clib.lcp_status_string(code)
+    assert clib.lcp_version() >= 10000
+
+
+def _err(clib):
+    return clib.lcp_last_error().decode()
+
+
+def test_stats_rejects_bad_arguments(clib):
+    f = clib.lcp_stats
+    outs = [FAKE] * 4
+    assert f(None, FAKE, 0, 4, 8, 8, 64, 1, *outs, None) == -1 and "non-NULL" in _err(clib)
+    assert f(FAKE, FAKE, 0, 4, 1, 8, 64, 1, *outs, None) == -1 and "H >= 2" in _err(clib)
+    assert f(FAKE, FAKE, 0, 1, 8, 8, 64, 1, *outs, None) == -1 and "M - ddof" in _err(clib)
+    assert f(FAKE, FAKE, 0, 4, 8, 8, 63, 1, *outs, None) == -1 and "member_stride" in _err(clib)
+    assert f(FAKE, FAKE, 2, 4, 8, 8, 64, 1, *outs, None) == -1 and "dtype" in _err(clib)
+    assert f(FAKE, FAKE, 0, 4, 8, 8, 64, 2, *outs, None) == -1 and "ddof" in _err(clib)
+
+
+def test_fused_map_mc_reject_bad_arguments(clib):
+    iso = (ctypes.c_float * 2)(0.0, 1.0)
+    fused = clib.lcp_fused
+    assert fused(FAKE, FAKE, 0, 4, 8, 8, 64, 1, 1.0, 0.0, iso, 2, FAKE, 0, None, None) == -1
+    assert "dx and dy" in _err(clib)
+    assert fused(FAKE, FAKE, 0, 4, 8, 8, 64, 1, 1.0, 1.0, iso, 0, FAKE, 0, None, None) == -1
+    assert fused(FAKE, FAKE, 0, 4, 8, 8, 64, 1, 1.0, 1.0, iso, 2, FAKE, 1, None, None) == -1  # bf16 output
+    assert fused(FAKE, FAKE, 0, 4, 8, 8, 64, 1, 1.0, 1.0, None, 2, FAKE, 0, None, None) == -1
+    assert clib.lcp_map(FAKE, FAKE, 8, 8, iso, 300, FAKE, 0, None, None) == -1
+    assert clib.lcp_divergence(FAKE, FAKE, FAKE, FAKE, 8, 8, -1.0, 1.0, FAKE, FAKE, None) == -1
+    mc = clib.lcp_mc
+    assert mc(0, FAKE, FAKE, FAKE, FAKE, None, None, 0, 0, 0, 8, 8, 1.0, 1.0, iso, 2, 0, 1, 0, FAKE, None, None) == -1
+    assert "n_samples" in _err(clib)
+    assert mc(0, FAKE, FAKE, FAKE, FAKE, None, None, 0, 0, 0, 8, 8, 1.0, 1.0, iso, 2, 10, 1, 0, None, None, None) == -1
+    assert mc(5, FAKE, FAKE, FAKE, FAKE, None, None, 0, 0, 0, 8, 8, 1.0, 1.0, iso, 2, 10, 1, 0, FAKE, None, None) == -1
+    assert mc(1, None, None, None, None, None, FAKE, 0, 4, 64, 8, 8, 1.0, 1.0, iso, 2, 10, 1, 0, FAKE, None, None) == -1
+    assert clib.lcp_philox_fill(0, 0, 0, 0, None, None) == 0  # empty request: nothing to do
+    assert clib.lcp_philox_fill(0, 0, 0, 10, None, None) == -1
+
+
+def test_product_package_never_reaches_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2510_01190_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
+                assert "lcp_oracle" not in src, f
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2510_01190_gb300 import _binding
+
+    monkeypatch.setattr(_binding, "_LIB", None)
+    monkeypatch.setattr(_binding, "library_path", lambda: str(tmp_path / "absent.so"))
+    with pytest.raises(_binding.LcpError):
+        _binding.load(build_if_stale=False)
