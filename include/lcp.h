@@ -126,7 +126,9 @@ lcp_status lcp_map(const float* mu_d, const float* var_d, int H, int W, const fl
  * and per-vertex probabilities stay on chip.  Same arguments and results as
  * the three calls in sequence (the mean is kept as member-0 shift plus FP32
  * offset internally, so it is at least as accurate as the unfused path).
- * K > 32 is processed in passes of 32 isovalues.
+ * K > 32 is processed in passes of 32 isovalues.  When the planes are 16-byte
+ * aligned and W and member_stride are multiples of 16 bytes, members stream
+ * through TMA copies into shared memory; otherwise through vector loads.
  */
 lcp_status lcp_fused(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
                      int64_t member_stride, int ddof, double dx, double dy, const float* iso, int K,
@@ -161,6 +163,16 @@ lcp_status lcp_mc(lcp_mc_mode mode, const float* mu_u, const float* var_u, const
                   int64_t member_stride, int H, int W, double dx, double dy, const float* iso, int K,
                   int64_t n_samples, uint64_t seed, uint64_t offset, uint32_t* counts,
                   float* lcp_out, lcp_stream_t stream);
+
+/*
+ * lcp_device_status - read (and optionally clear) the library's device status
+ * word on the current device.  Bit 0 is set when a bounded device-side wait
+ * (the TMA pipeline's mbarrier waits) gave up; the affected outputs are then
+ * undefined.  This call synchronises with the device (it copies one word).
+ * Returns LCP_ERR_TIMEOUT if any bit is set, LCP_OK otherwise; `flags` (host,
+ * may be NULL) receives the word; `reset` != 0 clears it.
+ */
+lcp_status lcp_device_status(uint32_t* flags, int reset);
 
 /*
  * lcp_philox_fill - the Monte Carlo generator's raw words, for testing and

@@ -26,6 +26,7 @@ __all__ = [
     "lcp_fused_host",
     "lcp_mc",
     "lcp_philox_fill",
+    "lcp_device_status",
     "mask_words_per_row",
     "unpack_mask",
     "LCP_F32",
@@ -57,6 +58,7 @@ _SIGNATURES = {
     "lcp_mc": (c_int, [c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_int, c_int, c_i64, c_int, c_int, c_double,
                        c_double, c_fp, c_int, c_i64, c_u64, c_u64, c_vp, c_vp, c_vp]),
     "lcp_philox_fill": (c_int, [c_u64, c_u32, c_u64, c_i64, c_vp, c_vp]),
+    "lcp_device_status": (c_int, [ctypes.POINTER(c_u32), c_int]),
 }
 
 
@@ -277,6 +279,15 @@ def lcp_philox_fill(seed: int, c1: int, offset: int, count: int, device="cuda"):
     _check(lib.lcp_philox_fill(int(seed) & (2**64 - 1), int(c1) & 0xFFFFFFFF, int(offset) & (2**64 - 1), int(count),
                                _ptr(out), _stream()))
     return out
+
+
+def lcp_device_status(reset: bool = False) -> int:
+    """The library's device status word (bit 0: a bounded device wait gave up).  Synchronising."""
+    flags = c_u32(0)
+    status = load().lcp_device_status(ctypes.byref(flags), int(reset))
+    if status not in (0, -4):
+        _check(status)
+    return int(flags.value)
 
 
 def unpack_mask(mask_words, w: int):

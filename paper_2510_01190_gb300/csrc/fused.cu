@@ -444,8 +444,18 @@ extern "C" lcp_status lcp_fused(const void* u, const void* v, lcp_dtype in_dtype
     if (p.ms > M) p.ms = 1;
     p.kbase = 0;
     p.n_ty = 1;
-    const bool in16 = aligned16(u) && aligned16(v);
     cudaStream_t st = (cudaStream_t)stream;
+    // The TMA row-march is opt-in (LCP_FUSED_TMA=1): on GB300 it measures a few
+    // percent slower than register streaming at K = 8 and more at K >= 16.
+    static const bool tma_enabled = [] {
+        const char* e = getenv("LCP_FUSED_TMA");
+        return e && e[0] == '1';
+    }();
+    if (tma_enabled) {
+        s = fused_tma(u, v, in_dtype, M, H, W, p.stride, ddof, dx, dy, iso, K, lcp_out, out_dtype, mask, st);
+        if (s != LCP_ERR_UNSUPPORTED) return s;
+    }
+    const bool in16 = aligned16(u) && aligned16(v);
     const bool f16 = out_dtype == LCP_F16;
     if (in_dtype == LCP_F32) {
         const bool vec = in16 && W % 4 == 0 && p.stride % 4 == 0;

@@ -180,6 +180,13 @@ inline lcp_status check_iso(const char* fn, const float* iso, int K) {
     return LCP_OK;
 }
 
+// TMA-pipeline variant of lcp_fused (fused_tma.cu).  Returns
+// LCP_ERR_UNSUPPORTED, having enqueued nothing, when the layout does not allow
+// TMA (alignment / strides); the caller then uses the register-streaming kernel.
+lcp_status fused_tma(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W, int64_t stride, int ddof,
+                     double dx, double dy, const float* iso, int K, void* out, lcp_dtype out_dtype, uint32_t* mask,
+                     cudaStream_t st);
+
 inline lcp_status check_spacing(const char* fn, double dx, double dy) {
     if (!(dx > 0.0) || !(dy > 0.0) || dx > 1e30 || dy > 1e30)
         return fail(LCP_ERR_ARG, "%s: dx and dy must be finite and > 0", fn);

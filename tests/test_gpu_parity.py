@@ -267,3 +267,45 @@ def test_mc_converges_to_closed_form(lib):
     c, e = _np(closed)[:, 1:-1, 1:-1], _np(est)[:, 1:-1, 1:-1]  # interior cells (independent vertices)
     se = np.sqrt(c * (1 - c) / s) + 1e-9
     assert np.abs((e - c) / se).max() < 5.5
+
+
+# ---------------------------------------------------------------------------
+# both fused variants (TMA pipeline and register streaming) on the same input
+# ---------------------------------------------------------------------------
+_VARIANT_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import paper_2510_01190_gb300 as lib
+from paper_2510_01190_gb300 import synth
+d = synth.fourier_ensemble(31, h=150, w=516, m=23, k=5)
+u = torch.from_numpy(d["u"]).cuda(); v = torch.from_numpy(d["v"]).cuda()
+lcp, mask = lib.lcp_fused(u, v, d["isovalues"], mask=True)
+np.save(sys.argv[2], lcp.cpu().numpy()); np.save(sys.argv[3], mask.cpu().numpy())
+"""
+
+
+def test_register_streaming_variant_matches_oracle(tmp_path):
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "variant.py"
+    script.write_text(_VARIANT_SCRIPT)
+    outs = {}
+    for tma in ("0", "1"):
+        env = dict(os.environ, LCP_FUSED_TMA=tma)
+        a, b = tmp_path / f"lcp{tma}.npy", tmp_path / f"mask{tma}.npy"
+        subprocess.run([sys.executable, str(script), root, str(a), str(b)], check=True, env=env, timeout=600)
+        outs[tma] = (np.load(a), np.load(b))
+    d = synth.fourier_ensemble(31, h=150, w=516, m=23, k=5)
+    ref = O.lcp_closed_form(d["u"], d["v"], 1.0, 1.0, d["isovalues"])
+    for tma in ("0", "1"):
+        assert np.max(np.abs(outs[tma][0] - ref["lcp"])) <= LCP_TOL
+    assert np.max(np.abs(outs["0"][0] - outs["1"][0])) <= 2e-6
+    assert np.array_equal(outs["0"][1], outs["1"][1])
+
+
+def test_device_status_clear_after_runs(lib):
+    torch.cuda.synchronize()
+    assert lib.lcp_device_status() == 0
