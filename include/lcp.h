@@ -135,6 +135,28 @@ lcp_status lcp_fused(const void* u, const void* v, lcp_dtype in_dtype, int M, in
                      void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, lcp_stream_t stream);
 
 /*
+ * lcp_fused_workspace_bytes / lcp_fused_ws - lcp_fused with a caller-provided
+ * device workspace (256-byte aligned, at least lcp_fused_workspace_bytes(M, H,
+ * W, in_dtype) bytes).  Same results as lcp_fused.  Each member byte is still
+ * read from HBM once: a flat, coalesced statistics stream leaves two 16-byte
+ * records per vertex (member-0 shift, shifted mean and variance of u and of v)
+ * in the workspace with an L2 keep-resident policy, and a second kernel,
+ * launched as its programmatic dependent, evaluates Eqs. 2/3 and the LCP of
+ * every cell from there, each of its blocks starting as soon as the records it
+ * reads are complete (per-band counters in the workspace, reset by the call
+ * with a memset node on `stream`).  Grids whose records exceed about 48 MB run
+ * in bands of rows with one halo row each side, so the workspace stays in L2
+ * and its size is bounded.  Calls sharing one workspace must not overlap in
+ * time.  workspace == NULL runs lcp_fused.
+ */
+size_t lcp_fused_workspace_bytes(int M, int H, int W, lcp_dtype in_dtype);
+
+lcp_status lcp_fused_ws(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
+                        int64_t member_stride, int ddof, double dx, double dy, const float* iso, int K,
+                        void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, void* workspace,
+                        size_t workspace_bytes, lcp_stream_t stream);
+
+/*
  * lcp_mc - classical Monte Carlo estimate of the LCP map (Sec. 3.2 and Sec. 4):
  * every sample is one realisation of the whole field; its divergence (Eq. 1,
  * same boundary rule) is tested per cell and isovalue, "crossing" meaning
@@ -167,8 +189,9 @@ lcp_status lcp_mc(lcp_mc_mode mode, const float* mu_u, const float* var_u, const
 /*
  * lcp_device_status - read (and optionally clear) the library's device status
  * word on the current device.  Bit 0 is set when a bounded device-side wait
- * (the TMA pipeline's mbarrier waits) gave up; the affected outputs are then
- * undefined.  This call synchronises with the device (it copies one word).
+ * (the TMA pipeline's mbarrier waits, the workspace path's waits for
+ * statistics rows) gave up; the affected outputs are then undefined.  This
+ * call synchronises with the device.
  * Returns LCP_ERR_TIMEOUT if any bit is set, LCP_OK otherwise; `flags` (host,
  * may be NULL) receives the word; `reset` != 0 clears it.
  */

@@ -23,6 +23,8 @@ __all__ = [
     "lcp_divergence",
     "lcp_map",
     "lcp_fused",
+    "lcp_fused_ws",
+    "lcp_fused_workspace_bytes",
     "lcp_fused_host",
     "lcp_mc",
     "lcp_philox_fill",
@@ -59,6 +61,9 @@ _SIGNATURES = {
                        c_double, c_fp, c_int, c_i64, c_u64, c_u64, c_vp, c_vp, c_vp]),
     "lcp_philox_fill": (c_int, [c_u64, c_u32, c_u64, c_i64, c_vp, c_vp]),
     "lcp_device_status": (c_int, [ctypes.POINTER(c_u32), c_int]),
+    "lcp_fused_workspace_bytes": (ctypes.c_size_t, [c_int, c_int, c_int, c_int]),
+    "lcp_fused_ws": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double, c_fp, c_int,
+                             c_vp, c_int, c_vp, c_vp, ctypes.c_size_t, c_vp]),
 }
 
 
@@ -204,6 +209,44 @@ def lcp_fused(u, v, isovalues, dx: float = 1.0, dy: float = 1.0, ddof: int = 1, 
     return out, mask_out
 
 
+def lcp_fused_workspace_bytes(m: int, h: int, w: int, dtype=torch.float32) -> int:
+    return int(load().lcp_fused_workspace_bytes(m, h, w, _dtype_code(dtype)))
+
+
+_WS = {}
+
+
+def _workspace(nbytes: int, device):
+    key = (str(device), torch.cuda.current_stream(device).cuda_stream)
+    buf = _WS.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        _WS[key] = buf
+    off = (-buf.data_ptr()) % 256
+    return buf, buf.data_ptr() + off
+
+
+def lcp_fused_ws(u, v, isovalues, dx: float = 1.0, dy: float = 1.0, ddof: int = 1, out_dtype=torch.float32,
+                 mask: bool = False, out=None, mask_out=None, workspace=None):
+    """``lcp_fused`` through the persistent dataflow kernel, with a device
+    workspace (a uint8 CUDA tensor of at least ``lcp_fused_workspace_bytes``;
+    by default one cached per device and stream).  Returns (lcp, mask_words|None)."""
+    m, h, w, stride = _members(u, v)
+    iso, k, iso_p = _iso(isovalues)
+    out, mask_out = _outputs(k, h, w, u.device, out_dtype, mask, out, mask_out)
+    lib = load()
+    need = int(lib.lcp_fused_workspace_bytes(m, h, w, _dtype_code(u.dtype)))
+    if workspace is None:
+        _, ws_ptr = _workspace(need, u.device)
+        ws_bytes = need
+    else:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    _check(lib.lcp_fused_ws(_ptr(u), _ptr(v), _dtype_code(u.dtype), m, h, w, stride, ddof, float(dx), float(dy),
+                            iso_p, k, _ptr(out), _dtype_code(out.dtype), _ptr(mask_out), c_vp(ws_ptr), ws_bytes,
+                            _stream()))
+    return out, mask_out
+
+
 class _HostStaging:
     """Device buffers reused by ``lcp_fused_host`` across calls of one shape."""
 
@@ -236,7 +279,7 @@ def lcp_fused_host(u_host, v_host, isovalues, dx: float = 1.0, dy: float = 1.0, 
     ud, vd, od, md = _STAGING.bufs
     ud.copy_(u_host, non_blocking=True)
     vd.copy_(v_host, non_blocking=True)
-    lcp_fused(ud, vd, iso, dx, dy, ddof, mask=md is not None, out=od, mask_out=md)
+    lcp_fused_ws(ud, vd, iso, dx, dy, ddof, mask=md is not None, out=od, mask_out=md)
     if out_host is None:
         out_host = torch.empty(od.shape, dtype=od.dtype, pin_memory=True)
     out_host.copy_(od, non_blocking=True)

@@ -510,15 +510,14 @@ lcp_status fused_tma(const void* u, const void* v, lcp_dtype in_dtype, int M, in
 
 }  // namespace lcp
 
-extern "C" lcp_status lcp_device_status(uint32_t* flags, int reset) {
+namespace lcp {
+uint32_t read_tma_status(bool reset) {
     uint32_t f = 0;
-    if (cudaMemcpyFromSymbol(&f, lcp::g_fused_status, sizeof(f)) != cudaSuccess)
-        return lcp::fail(LCP_ERR_CUDA, "lcp_device_status: cannot read the status word");
+    cudaMemcpyFromSymbol(&f, g_fused_status, sizeof(f));
     if (reset) {
         const uint32_t z = 0;
-        if (cudaMemcpyToSymbol(lcp::g_fused_status, &z, sizeof(z)) != cudaSuccess)
-            return lcp::fail(LCP_ERR_CUDA, "lcp_device_status: cannot reset the status word");
+        cudaMemcpyToSymbol(g_fused_status, &z, sizeof(z));
     }
-    if (flags) *flags = f;
-    return f ? lcp::fail(LCP_ERR_TIMEOUT, "a bounded device wait gave up (flags 0x%x)", f) : LCP_OK;
+    return f;
 }
+}  // namespace lcp

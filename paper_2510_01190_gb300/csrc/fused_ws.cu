@@ -1,0 +1,667 @@
+// lcp_fused_ws: the closed-form path in two kernels that share an L2-resident
+// workspace (statistics, Sec. 3.1; Eqs. 2/3 with the one-sided boundary rule;
+// the LCP of every cell, Sec. 3.1 last paragraph).
+//
+// 1) stats_ws_kernel: a flat, fully coalesced stream over the member planes --
+//    each thread owns VEC consecutive vertices and keeps 16 independent
+//    16-byte loads in flight, the access pattern that runs near HBM peak.  Per
+//    vertex and component it stores one 16-byte record (x0, delta, var, 0):
+//    member 0, the FP32 mean of the values shifted by member 0, and the
+//    variance.  Member loads carry an L2 evict-first policy and the record
+//    stores evict-last, so the 32 bytes per vertex stay in the 129 MB L2.
+// 2) lcp_rows_kernel: a tile of 8 cell rows x 256 cell columns, one vertex
+//    column per thread, marching down the rows with a sliding register window
+//    (own column's u record, whose horizontal neighbours come by warp shuffle;
+//    v records of rows j-1, j, j+1), the next row always in flight.  Phase A:
+//    each thread forms the divergence Gaussian of its vertex and evaluates one
+//    erfc per isovalue into shared memory (the tile's extra right vertex is
+//    loaded by four lanes of the last warp, gathered by shuffle, and its
+//    isovalues shared out over the lanes).  Phase B: each thread forms its
+//    cell's horizontal products p_i p_{i+1}, q_i q_{i+1}, closes the cell with
+//    the previous row's products (kept in registers), stores it coalesced, and
+//    the warp ballots the mean-field crossing bits into whole mask words.  The
+//    kernel is compiled for exact isovalue counts 1, 2, 4, 8, 16, 32 (other K
+//    run as a sum of such passes), so the isovalue loop has no guards.
+//
+// Overlap.  The statistics grid triggers its programmatic dependents as each
+// block starts and, after storing, counts itself into per-row-band counters in
+// the workspace (fence, then atomic add).  The LCP grid, launched as its
+// programmatic dependent, therefore starts as soon as every statistics block
+// is resident (its last wave), and each LCP block waits -- bounded, with
+// backoff -- only for the statistics rows of its own band.  The wait cannot
+// deadlock: every block it waits for is already running.
+//
+// Grids whose records would not fit comfortably in L2 are processed in bands
+// of rows (records of the band plus one halo row on each side, then its
+// cells), so the workspace never spills to HBM.
+#include <mutex>
+
+#include "lcp_common.cuh"
+
+namespace lcp {
+
+__device__ unsigned int g_ws_status;  // bit 0: an LCP block's dependency wait gave up
+
+namespace {
+
+constexpr int kST = 256;           // stats kernel threads
+constexpr int kRT = 256;           // LCP kernel threads = cell columns per tile
+constexpr int kTR = 8;             // cell rows per LCP tile
+constexpr int kMaxKPass = 32;      // isovalues per LCP launch
+constexpr size_t kL2Budget = 48ull << 20;  // workspace bytes a band may occupy
+constexpr long long kWaitBudget = 4000000000ll;  // clock cycles (~2 s) before a dependency wait gives up
+
+// Statistics blocks [blo, bhi] of the statistics grid that cover the rows LCP
+// row band `by` needs (its vertex rows and one halo row each side).  The same
+// function decides what a statistics block signals and what an LCP block waits
+// for, so the two sides agree by construction.
+__device__ __forceinline__ void band_blocks(int64_t n_begin, int sv, int W, int H, int r_begin, int r_end, int by,
+                                            int& blo, int& bhi) {
+    const int a = r_begin + by * kTR, e = min(a + kTR, r_end);
+    const int lo = max(a - 1, 0), hi = min(e + 1, H - 1);
+    blo = (int)(((int64_t)lo * W - n_begin) / sv);
+    bhi = (int)((((int64_t)hi + 1) * W - 1 - n_begin) / sv);
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// ---- cache-policy loads / stores ------------------------------------------
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float4 ld_stream_f4(const float* p, uint64_t pol) {
+    float4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint4 ld_stream_u4(const void* p, uint64_t pol) {
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ void st_keep_f4(float* p, float4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_keep_f1(float* p, float v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+
+template <typename T, int VEC>
+struct SLoad;
+template <>
+struct SLoad<float, 4> {
+    using raw_t = float4;
+    static __device__ __forceinline__ raw_t load(const float* p, uint64_t pol) { return ld_stream_f4(p, pol); }
+    static __device__ __forceinline__ void cvt(const raw_t& r, float* x) { x[0] = r.x; x[1] = r.y; x[2] = r.z; x[3] = r.w; }
+};
+template <>
+struct SLoad<__nv_bfloat16, 8> {
+    using raw_t = uint4;
+    static __device__ __forceinline__ raw_t load(const __nv_bfloat16* p, uint64_t pol) { return ld_stream_u4(p, pol); }
+    static __device__ __forceinline__ void cvt(const raw_t& r, float* x) { Loader<__nv_bfloat16, 8>::cvt(r, x); }
+};
+template <typename T>
+__device__ __forceinline__ float load1(const T* p) {
+    float x;
+    Loader<T, 1>::cvt(Loader<T, 1>::load(p), &x);
+    return x;
+}
+
+// ---- 1) statistics stream ----------------------------------------------------
+// Workspace record of one vertex and component: float4 (x0, delta, var, 0) --
+// member 0, FP32 mean of the values shifted by member 0, variance -- so that
+// the LCP kernel reads a vertex's component with one 16-byte load.  Two
+// record planes (u, v) of `ws_rows` rows x W vertices.
+struct StatsWsParams {
+    const void* u;
+    const void* v;
+    int64_t stride;
+    int M, W, ddof;
+    int64_t n_begin, n_end;  // flat vertex range [n_begin, n_end) of this band (member-plane index)
+    int row0;                // first row of the band (workspace row 0)
+    float4* st;              // record planes: u at st, v at st + ps
+    int64_t ps;              // plane stride in records
+    int vecload;
+    uint32_t* dep;           // per LCP row band: statistics blocks completed
+    int H, r_begin, r_end, nby;
+};
+
+__device__ __forceinline__ void store_stats(const StatsWsParams& p, int64_t n, const float* x0, const float* s1,
+                                            const float* s2, int comp, uint64_t keep, int cnt) {
+    const float fm = (float)p.M, fdof = (float)(p.M - p.ddof);
+    // records are flat-indexed from the band's first row: (j - row0) * W + i = n - row0 * W
+    float4* base = p.st + comp * p.ps + (n - (int64_t)p.row0 * p.W);
+    for (int e = 0; e < cnt; ++e) {
+        const float dl = s1[e] / fm;
+        float vv = (s2[e] - s1[e] * dl) / fdof;
+        vv = vv < 0.f ? 0.f : vv;  // NaN stays NaN
+        st_keep_f4(reinterpret_cast<float*>(base + e), make_float4(x0[e], dl, vv, 0.f), keep);
+    }
+}
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kST) stats_ws_kernel(const __grid_constant__ StatsWsParams p) {
+    const T* __restrict__ u = reinterpret_cast<const T*>(p.u);
+    const T* __restrict__ v = reinterpret_cast<const T*>(p.v);
+    const uint64_t pol = policy_evict_first();
+    const uint64_t keep = policy_evict_last();
+    // Every block of this grid is resident once all have executed this: the
+    // dependent LCP grid may then launch and wait on the per-band counters.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int64_t n0 = p.n_begin + ((int64_t)blockIdx.x * kST + threadIdx.x) * VEC;
+    const int M = p.M;
+    if (n0 < p.n_end) {
+        if (p.vecload && n0 + VEC <= p.n_end) {
+            using L = SLoad<T, VEC>;
+            float x0u[VEC], x0v[VEC], s1u[VEC], s2u[VEC], s1v[VEC], s2v[VEC];
+            L::cvt(L::load(u + n0, pol), x0u);
+            L::cvt(L::load(v + n0, pol), x0v);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) s1u[e] = s2u[e] = s1v[e] = s2v[e] = 0.f;
+            auto acc = [&](const typename L::raw_t& ru, const typename L::raw_t& rv) {
+                float a[VEC], b[VEC];
+                L::cvt(ru, a);
+                L::cvt(rv, b);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const float du = a[e] - x0u[e], dv = b[e] - x0v[e];
+                    s1u[e] += du;
+                    s2u[e] = fmaf(du, du, s2u[e]);
+                    s1v[e] += dv;
+                    s2v[e] = fmaf(dv, dv, s2v[e]);
+                }
+            };
+            constexpr int UNROLL = VEC >= 8 ? 4 : 8;
+            int m = 1;
+            for (; m + UNROLL <= M; m += UNROLL) {
+                typename L::raw_t ru[UNROLL], rv[UNROLL];
+#pragma unroll
+                for (int q = 0; q < UNROLL; ++q) {
+                    ru[q] = L::load(u + (int64_t)(m + q) * p.stride + n0, pol);
+                    rv[q] = L::load(v + (int64_t)(m + q) * p.stride + n0, pol);
+                }
+#pragma unroll
+                for (int q = 0; q < UNROLL; ++q) acc(ru[q], rv[q]);
+            }
+            for (; m < M; ++m) acc(L::load(u + (int64_t)m * p.stride + n0, pol), L::load(v + (int64_t)m * p.stride + n0, pol));
+            store_stats(p, n0, x0u, s1u, s2u, 0, keep, VEC);
+            store_stats(p, n0, x0v, s1v, s2v, 1, keep, VEC);
+        } else {
+            const int64_t n_end = min(n0 + VEC, p.n_end);
+            for (int64_t n = n0; n < n_end; ++n) {
+                float x0u = load1(u + n), x0v = load1(v + n);
+                float a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;
+                for (int m = 1; m < M; ++m) {
+                    const float du = load1(u + (int64_t)m * p.stride + n) - x0u;
+                    const float dv = load1(v + (int64_t)m * p.stride + n) - x0v;
+                    a1 += du;
+                    a2 = fmaf(du, du, a2);
+                    b1 += dv;
+                    b2 = fmaf(dv, dv, b2);
+                }
+                store_stats(p, n, &x0u, &a1, &a2, 0, keep, 1);
+                store_stats(p, n, &x0v, &b1, &b2, 1, keep, 1);
+            }
+        }
+    }
+    // publish: this block's statistics are stored; count it for every LCP row
+    // band whose rows it covers
+    __syncthreads();
+    if (threadIdx.x == 0 && p.dep) {
+        __threadfence();
+        constexpr int sv = kST * VEC;
+        const int64_t f0 = p.n_begin + (int64_t)blockIdx.x * sv;
+        const int64_t f1 = min(f0 + sv, p.n_end) - 1;
+        const int rs0 = (int)(f0 / p.W), rs1 = (int)(f1 / p.W);
+        const int lo = max(0, (rs0 - 1 - p.r_begin) / kTR - 1), hi = min(p.nby - 1, (rs1 + 1 - p.r_begin) / kTR + 1);
+        for (int by = lo; by <= hi; ++by) {
+            int blo, bhi;
+            band_blocks(p.n_begin, sv, p.W, p.H, p.r_begin, p.r_end, by, blo, bhi);
+            if ((int)blockIdx.x >= blo && (int)blockIdx.x <= bhi) atomicAdd(&p.dep[by], 1u);
+        }
+    }
+}
+
+// ---- 2) divergence + LCP from the workspace -----------------------------------
+struct RowsParams {
+    const float4* st;  // record planes (u at st, v at st + ps); record row 0 = grid row `row0`
+    int64_t ps;
+    int row0;
+    int H, W;            // full grid
+    int r_begin, r_end;  // cell rows [r_begin, r_end) of this band (grid coordinates)
+    Spacing sp;
+    void* out;
+    uint32_t* mask;
+    int n_words;
+    int kbase;            // index of this pass's first isovalue in the output
+    const uint32_t* dep;  // per row band: statistics blocks completed
+    int64_t n_begin;      // statistics grid geometry, to recompute each band's requirement
+    int sv;
+};
+
+// Records are read through L2 (ld.global.cg): the statistics grid may still be
+// writing other rows of the workspace, so no stale L1 line may be used.
+__device__ __forceinline__ float4 ld_rec(const float4* p) { return __ldcg(p); }
+
+__device__ __forceinline__ float4 shfl_rec(float4 a, int src) {
+    return make_float4(__shfl_sync(0xFFFFFFFFu, a.x, src), __shfl_sync(0xFFFFFFFFu, a.y, src),
+                       __shfl_sync(0xFFFFFFFFu, a.z, src), 0.f);
+}
+
+// Records of the tile's extra right vertex ix at row j, one per lane of the
+// last warp: lane 0 u at i+, lane 1 u at i-, lane 2 v at j+, lane 3 v at j-.
+__device__ __forceinline__ float4 load_extra(const RowsParams& p, int j, int lane, int ix) {
+    if (lane >= 4) return make_float4(0.f, 0.f, 0.f, 0.f);
+    int row = j, col = ix, comp = 0;
+    if (lane == 0) col = min(ix + 1, p.W - 1);
+    if (lane == 1) col = max(ix - 1, 0);
+    if (lane == 2) row = min(j + 1, p.H - 1), comp = 1;
+    if (lane == 3) row = max(j - 1, 0), comp = 1;
+    return ld_rec(p.st + comp * p.ps + (int64_t)(row - p.row0) * p.W + col);
+}
+
+// (P(D < c), P(D >= c)) of a vertex (mu, s = 1/(sigma sqrt 2)); below = mu < c.
+// Zero variance takes the argument +-1e4, whose erfc underflows to 0, giving the
+// indicator [mu < c] (also when mu == c) without a separate branch.
+__device__ __forceinline__ float2 vertex_pq(float mu, float s, bool zero, float c, bool below) {
+    float t = (mu - c) * s;
+    if (zero) t = below ? -1.0e4f : 1.0e4f;
+    const float e = half_erfc_nonneg(fabsf(t));
+    const bool pos = t >= 0.0f;  // NaN: false, and both results stay NaN
+    return make_float2(pos ? e : 1.0f - e, pos ? 1.0f - e : e);
+}
+
+// Clamp to [0, 1] with NaN propagated (max.NaN / min.NaN).
+__device__ __forceinline__ float clamp01_nan(float x) {
+    float r;
+    asm("max.NaN.f32 %0, %1, 0f00000000;" : "=f"(r) : "f"(x));
+    asm("min.NaN.f32 %0, %0, 0f3F800000;" : "+f"(r));
+    return r;
+}
+
+// One tile: 8 cell rows x 256 cell columns, one vertex column per thread; KX
+// isovalues exactly (other counts run as sums of such passes); MASK selects the
+// mean-field bits.
+template <int KX, bool MASK, typename OutT>
+__global__ void __launch_bounds__(kRT, KX <= 8 ? 3 : (KX <= 16 ? 2 : 1))
+    lcp_rows_kernel(const __grid_constant__ RowsParams p, const __grid_constant__ IsoParams iso) {
+    constexpr int NV = kRT + 1;                      // vertices per tile row
+    extern __shared__ __align__(16) float2 pq[];     // [KX][NV] (P(D < c), P(D >= c)) of the current row
+    uint32_t* cls = reinterpret_cast<uint32_t*>(pq + KX * NV);  // [NV] bit k: mu_d < c_k
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int H = p.H, W = p.W, Hc = H - 1, Wc = W - 1;
+    const int c0 = blockIdx.x * kRT;
+    const int a = p.r_begin + blockIdx.y * kTR;
+    if (a >= p.r_end) return;
+    const int e = min(a + kTR, p.r_end);  // cells [a, e), vertex rows a..e
+    if (p.dep) {  // wait (bounded) until the statistics rows this band reads are complete
+        if (t == 0) {
+            int blo, bhi;
+            band_blocks(p.n_begin, p.sv, W, H, p.r_begin, p.r_end, blockIdx.y, blo, bhi);
+            const uint32_t need = (uint32_t)(bhi - blo + 1);
+            const long long t0 = clock64();
+            while (ld_acquire(&p.dep[blockIdx.y]) < need) {
+                if (clock64() - t0 > kWaitBudget) {
+                    atomicOr(&g_ws_status, 1u);
+                    break;
+                }
+                __nanosleep(200);
+            }
+        }
+        __syncthreads();
+    }
+    const bool last_warp = warp == kRT / 32 - 1;
+    const int i = c0 + t, ic = min(i, W - 1);
+    const bool ok = i < Wc;
+    const bool one_sided_x = ic == 0 || ic == W - 1;
+    const float sx = one_sided_x ? p.sp.sx1 : p.sp.sx2, sxq = one_sided_x ? p.sp.sx1q : p.sp.sx2q;
+    const bool edge_lane = lane == 0 || lane == 31;
+    const int iedge = lane == 0 ? max(ic - 1, 0) : min(ic + 1, W - 1);  // warp-edge neighbour column
+    const int ix = min(c0 + kRT, W - 1);                                  // the tile's extra right vertex
+    const bool one_sided_xx = ix == 0 || ix == W - 1;
+    const float sx_x = one_sided_xx ? p.sp.sx1 : p.sp.sx2, sxq_x = one_sided_xx ? p.sp.sx1q : p.sp.sx2q;
+    const int wi = (c0 >> 5) + warp;
+    const bool word_writer = MASK && lane == 0 && wi < p.n_words;
+    float c[KX];
+#pragma unroll
+    for (int k = 0; k < KX; ++k) c[k] = iso.c[k];
+
+    // sliding window: u of the current row (own column; warp-edge lanes also the
+    // neighbour column), v of rows j-1, j, j+1; the next row always in flight
+    const float4* urow = p.st + (int64_t)(a - p.row0) * W;
+    const float4* vpl = p.st + p.ps;
+    float4 U = ld_rec(urow + ic), UE = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (edge_lane) UE = ld_rec(urow + iedge);
+    float4 VM = ld_rec(vpl + (int64_t)(max(a - 1, 0) - p.row0) * W + ic);
+    float4 V0 = ld_rec(vpl + (int64_t)(a - p.row0) * W + ic);
+    float4 VP = ld_rec(vpl + (int64_t)(min(a + 1, H - 1) - p.row0) * W + ic);
+    float4 X = last_warp ? load_extra(p, a, lane, ix) : make_float4(0.f, 0.f, 0.f, 0.f);
+
+    float ph_prev[KX], qh_prev[KX];
+    uint32_t b0_prev = 0, b1_prev = 0;
+    const int64_t plane = (int64_t)Hc * Wc, mplane = (int64_t)Hc * p.n_words;
+    OutT* po = reinterpret_cast<OutT*>(p.out) + (int64_t)p.kbase * plane + (int64_t)(a - 1) * Wc + i;
+    uint32_t* pm = MASK ? p.mask + ((int64_t)p.kbase * Hc + (a - 1)) * p.n_words + wi : nullptr;
+    for (int j = a; j <= e; ++j) {
+        const float4 Uc = U, UEc = UE, Xc = X;
+        float4 Vn = VP;
+        if (j < e) {  // next row, in flight while this row is evaluated
+            urow += W;
+            U = ld_rec(urow + ic);
+            if (edge_lane) UE = ld_rec(urow + iedge);
+            Vn = ld_rec(vpl + (int64_t)(min(j + 2, H - 1) - p.row0) * W + ic);
+            if (last_warp) X = load_extra(p, j + 1, lane, ix);
+        }
+        // divergence Gaussian of this thread's vertex (Eqs. 2/3, one-sided at the edges)
+        float4 L = make_float4(__shfl_up_sync(0xFFFFFFFFu, Uc.x, 1), __shfl_up_sync(0xFFFFFFFFu, Uc.y, 1),
+                               __shfl_up_sync(0xFFFFFFFFu, Uc.z, 1), 0.f);
+        float4 R = make_float4(__shfl_down_sync(0xFFFFFFFFu, Uc.x, 1), __shfl_down_sync(0xFFFFFFFFu, Uc.y, 1),
+                               __shfl_down_sync(0xFFFFFFFFu, Uc.z, 1), 0.f);
+        if (lane == 0) L = UEc;
+        if (lane == 31) R = UEc;
+        if (ic == 0) L = Uc;
+        if (ic == W - 1) R = Uc;
+        const bool one_sided_y = j == 0 || j == H - 1;
+        const float sy = one_sided_y ? p.sp.sy1 : p.sp.sy2, syq = one_sided_y ? p.sp.sy1q : p.sp.sy2q;
+        const float4 Vlo = j > 0 ? VM : V0;
+        const float4 Vhi = j < H - 1 ? VP : V0;
+        const float mu = fmaf((R.x - L.x) + (R.y - L.y), sx, ((Vhi.x - Vlo.x) + (Vhi.y - Vlo.y)) * sy);
+        const float var = fmaf(R.z + L.z, sxq, (Vhi.z + Vlo.z) * syq);
+        // phase A: its (p, q) and class bit for every isovalue
+        {
+            const bool zero = var == 0.0f;
+            const float s = rsqrtf(2.0f * var);
+            uint32_t b = 0;
+#pragma unroll
+            for (int k = 0; k < KX; ++k) {
+                const bool below = mu < c[k];
+                pq[k * NV + t] = vertex_pq(mu, s, zero, c[k], below);
+                b |= (uint32_t)below << k;
+            }
+            cls[t] = b;
+        }
+        if (last_warp) {  // the extra right vertex: gathered from lanes 0-3, isovalues spread over the lanes
+            const float4 up = shfl_rec(Xc, 0), ul = shfl_rec(Xc, 1), vh = shfl_rec(Xc, 2), vl = shfl_rec(Xc, 3);
+            const float mux = fmaf((up.x - ul.x) + (up.y - ul.y), sx_x, ((vh.x - vl.x) + (vh.y - vl.y)) * sy);
+            const float varx = fmaf(up.z + ul.z, sxq_x, (vh.z + vl.z) * syq);
+            float cl = 0.0f;
+#pragma unroll
+            for (int k = 0; k < KX; ++k)
+                if (k == lane) cl = c[k];
+            const bool below = mux < cl;
+            if (lane < KX) pq[lane * NV + kRT] = vertex_pq(mux, rsqrtf(2.0f * varx), varx == 0.0f, cl, below);
+            const uint32_t bx = __ballot_sync(0xFFFFFFFFu, lane < KX && below);
+            if (lane == 0) cls[kRT] = bx;
+        }
+        __syncthreads();
+        // phase B: close the cells of row j - 1
+        const uint32_t b0 = cls[t], b1 = cls[t + 1];
+        if (j > a) {
+            po += Wc;
+            if (MASK) pm += p.n_words;
+            // bit k: the cell's four vertices are not all on one side of c_k
+            const uint32_t cross = ok ? ((b0_prev | b1_prev | b0 | b1) & ~(b0_prev & b1_prev & b0 & b1)) : 0u;
+            OutT* o = po;
+            uint32_t* m = pm;
+#pragma unroll
+            for (int k = 0; k < KX; ++k) {
+                const float2 v0 = pq[k * NV + t], v1 = pq[k * NV + t + 1];
+                const float ph = v0.x * v1.x, qh = v0.y * v1.y;
+                const float lcp = fmaf(-qh_prev[k], qh, fmaf(-ph_prev[k], ph, 1.0f));
+                if (ok) *o = to_out<OutT>(clamp01_nan(lcp));
+                o += plane;
+                if (MASK) {
+                    const uint32_t word = __ballot_sync(0xFFFFFFFFu, (cross >> k) & 1u);
+                    if (word_writer) *m = word;
+                    m += mplane;
+                }
+                ph_prev[k] = ph;
+                qh_prev[k] = qh;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < KX; ++k) {
+                const float2 v0 = pq[k * NV + t], v1 = pq[k * NV + t + 1];
+                ph_prev[k] = v0.x * v1.x;
+                qh_prev[k] = v0.y * v1.y;
+            }
+        }
+        b0_prev = b0;
+        b1_prev = b1;
+        VM = V0;
+        V0 = VP;
+        VP = Vn;
+        __syncthreads();
+    }
+}
+
+// ---- host ----------------------------------------------------------------------
+struct Layout {
+    int band_rows;       // cell rows per band
+    int ws_rows;         // record rows per plane (band + halo)
+    int nby;             // LCP row bands (counters) per band
+    size_t ctr_bytes;    // counter header (256-byte multiple)
+    size_t plane_bytes;  // one record plane (padded)
+    size_t total;
+};
+
+Layout layout(int H, int W) {
+    Layout L;
+    const size_t row_bytes = (size_t)2 * W * sizeof(float4);
+    long rows = (long)(kL2Budget / row_bytes) - 2;
+    if (rows < kTR) rows = kTR;
+    if (rows >= H - 1) {
+        L.band_rows = H - 1;
+        L.ws_rows = H;
+    } else {
+        L.band_rows = (int)(rows / kTR) * kTR;
+        L.ws_rows = L.band_rows + 3;
+    }
+    L.nby = (L.band_rows + kTR - 1) / kTR;
+    L.ctr_bytes = ((size_t)L.nby * 4 + 255) & ~(size_t)255;
+    L.plane_bytes = ((size_t)L.ws_rows * W * sizeof(float4) + 255) & ~(size_t)255;
+    L.total = L.ctr_bytes + 2 * L.plane_bytes;
+    return L;
+}
+
+template <int KX, bool MASK, typename OutT>
+lcp_status launch_rows_k(const RowsParams& p, const IsoParams& ip, cudaStream_t st, bool pdl) {
+    auto kern = lcp_rows_kernel<KX, MASK, OutT>;
+    const size_t smem = (size_t)KX * (kRT + 1) * sizeof(float2) + (kRT + 1) * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        static std::mutex mu;
+        static bool set[64] = {false};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < 64 && !set[dev]) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                return fail(LCP_ERR_CUDA, "lcp_fused_ws: %zu bytes of shared memory not available", smem);
+            set[dev] = true;
+        }
+    }
+    const int rows = p.r_end - p.r_begin;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.W - 1 + kRT - 1) / kRT, (rows + kTR - 1) / kTR);
+    cfg.blockDim = dim3(kRT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (pdl) {
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, p, ip);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LCP_ERR_CUDA, "lcp_fused_ws: LCP kernel launch failed: %s", cudaGetErrorString(e));
+    }
+    return LCP_OK;
+}
+
+template <bool MASK, typename OutT>
+lcp_status launch_rows_chunk(const RowsParams& p, const IsoParams& ip, cudaStream_t st, bool pdl) {
+    switch (ip.K) {
+        case 1: return launch_rows_k<1, MASK, OutT>(p, ip, st, pdl);
+        case 2: return launch_rows_k<2, MASK, OutT>(p, ip, st, pdl);
+        case 4: return launch_rows_k<4, MASK, OutT>(p, ip, st, pdl);
+        case 8: return launch_rows_k<8, MASK, OutT>(p, ip, st, pdl);
+        case 16: return launch_rows_k<16, MASK, OutT>(p, ip, st, pdl);
+        case 32: return launch_rows_k<32, MASK, OutT>(p, ip, st, pdl);
+    }
+    return fail(LCP_ERR_UNSUPPORTED, "lcp_fused_ws: isovalue chunk %d", ip.K);
+}
+
+// Isovalues in passes whose sizes are the binary digits of K (largest first,
+// at most 32 each): every pass runs a kernel specialised for its exact count.
+template <typename OutT>
+lcp_status launch_rows(const RowsParams& p0, const float* iso, int K, cudaStream_t st) {
+    RowsParams p = p0;
+    int kb = 0;
+    bool first = true;
+    while (kb < K) {
+        int chunk = 32;
+        while (chunk > K - kb) chunk >>= 1;
+        IsoParams ip;
+        ip.K = chunk;
+        for (int k = 0; k < chunk; ++k) ip.c[k] = iso[kb + k];
+        p.kbase = kb;
+        const lcp_status s = p.mask ? launch_rows_chunk<true, OutT>(p, ip, st, first)
+                                    : launch_rows_chunk<false, OutT>(p, ip, st, first);
+        if (s != LCP_OK) return s;
+        kb += chunk;
+        first = false;
+    }
+    return LCP_OK;
+}
+
+template <typename T, int VEC>
+lcp_status run(const void* u, const void* v, int M, int H, int W, int64_t stride, int ddof, double dx, double dy,
+               const float* iso, int K, void* out, lcp_dtype out_dtype, uint32_t* mask, void* ws, bool vecload,
+               cudaStream_t st) {
+    const Layout L = layout(H, W);
+    const int Hc = H - 1;
+    uint32_t* dep = reinterpret_cast<uint32_t*>(ws);
+    float4* rec = reinterpret_cast<float4*>(reinterpret_cast<char*>(ws) + L.ctr_bytes);
+    for (int r0 = 0; r0 < Hc; r0 += L.band_rows) {
+        const int r1 = min(r0 + L.band_rows, Hc);  // cells [r0, r1): vertex rows r0..r1, statistics r0-1..r1+1
+        const int s0 = max(r0 - 1, 0), s1 = min(r1 + 1, H - 1);
+        const int nby = (r1 - r0 + kTR - 1) / kTR;
+        // counters start at zero for every band (the previous band's cells are done: stream order)
+        if (cudaMemsetAsync(dep, 0, (size_t)nby * 4, st) != cudaSuccess)
+            return fail(LCP_ERR_CUDA, "lcp_fused_ws: counter reset failed");
+        StatsWsParams sp;
+        sp.u = u;
+        sp.v = v;
+        sp.stride = stride;
+        sp.M = M;
+        sp.W = W;
+        sp.ddof = ddof;
+        sp.n_begin = (int64_t)s0 * W;
+        sp.n_end = (int64_t)(s1 + 1) * W;
+        sp.row0 = s0;
+        sp.st = rec;
+        sp.ps = (int64_t)(L.plane_bytes / sizeof(float4));
+        // the vertex groups must stay 16-byte aligned from the band's first vertex
+        sp.vecload = vecload && (sp.n_begin % VEC) == 0;
+        sp.dep = dep;
+        sp.H = H;
+        sp.r_begin = r0;
+        sp.r_end = r1;
+        sp.nby = nby;
+        const int64_t groups = (sp.n_end - sp.n_begin + VEC - 1) / VEC;
+        stats_ws_kernel<T, VEC><<<(unsigned)((groups + kST - 1) / kST), kST, 0, st>>>(sp);
+        lcp_status s = check_launch("lcp_fused_ws (statistics)");
+        if (s != LCP_OK) return s;
+        RowsParams rp;
+        rp.st = rec;
+        rp.ps = sp.ps;
+        rp.row0 = s0;
+        rp.H = H;
+        rp.W = W;
+        rp.r_begin = r0;
+        rp.r_end = r1;
+        rp.sp = make_spacing(dx, dy);
+        rp.out = out;
+        rp.mask = mask;
+        rp.n_words = (W - 1 + 31) / 32;
+        rp.kbase = 0;
+        rp.dep = dep;
+        rp.n_begin = sp.n_begin;
+        rp.sv = kST * VEC;
+        s = out_dtype == LCP_F16 ? launch_rows<__half>(rp, iso, K, st) : launch_rows<float>(rp, iso, K, st);
+        if (s != LCP_OK) return s;
+    }
+    return LCP_OK;
+}
+
+}  // namespace
+
+uint32_t read_ws_status(bool reset) {
+    uint32_t f = 0;
+    cudaMemcpyFromSymbol(&f, g_ws_status, sizeof(f));
+    if (reset) {
+        const uint32_t z = 0;
+        cudaMemcpyToSymbol(g_ws_status, &z, sizeof(z));
+    }
+    return f;
+}
+
+}  // namespace lcp
+
+using namespace lcp;
+
+extern "C" size_t lcp_fused_workspace_bytes(int M, int H, int W, lcp_dtype in_dtype) {
+    (void)in_dtype;
+    if (H < 2 || W < 2 || M < 1) return 0;
+    return layout(H, W).total;
+}
+
+extern "C" lcp_status lcp_fused_ws(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
+                                   int64_t member_stride, int ddof, double dx, double dy, const float* iso, int K,
+                                   void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, void* workspace,
+                                   size_t workspace_bytes, lcp_stream_t stream) {
+    if (!workspace)
+        return lcp_fused(u, v, in_dtype, M, H, W, member_stride, ddof, dx, dy, iso, K, lcp_out, out_dtype, mask,
+                         stream);
+    lcp_status s = check_members("lcp_fused_ws", u, v, in_dtype, M, H, W, member_stride, ddof);
+    if (s != LCP_OK) return s;
+    if ((s = check_iso("lcp_fused_ws", iso, K)) != LCP_OK) return s;
+    if ((s = check_spacing("lcp_fused_ws", dx, dy)) != LCP_OK) return s;
+    if (!lcp_out) return fail(LCP_ERR_ARG, "lcp_fused_ws: NULL output");
+    if (out_dtype != LCP_F32 && out_dtype != LCP_F16) return fail(LCP_ERR_ARG, "lcp_fused_ws: out dtype must be F32 or F16");
+    if ((uintptr_t)mask & 3) return fail(LCP_ERR_ARG, "lcp_fused_ws: mask must be 4-byte aligned");
+    if ((uintptr_t)workspace & 255) return fail(LCP_ERR_ARG, "lcp_fused_ws: workspace must be 256-byte aligned");
+    const Layout L = layout(H, W);
+    if (workspace_bytes < L.total)
+        return fail(LCP_ERR_ARG, "lcp_fused_ws: workspace too small (%zu < %zu bytes)", workspace_bytes, L.total);
+    if ((H - 1 + kTR - 1) / kTR > 65535) return fail(LCP_ERR_UNSUPPORTED, "lcp_fused_ws: H too large");
+    const int64_t stride = M > 1 ? member_stride : (int64_t)H * W;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool in16 = aligned16(u) && aligned16(v);
+    if (in_dtype == LCP_F32)
+        return run<float, 4>(u, v, M, H, W, stride, ddof, dx, dy, iso, K, lcp_out, out_dtype, mask, workspace,
+                             in16 && stride % 4 == 0, st);
+    return run<__nv_bfloat16, 8>(u, v, M, H, W, stride, ddof, dx, dy, iso, K, lcp_out, out_dtype, mask, workspace,
+                                 in16 && stride % 8 == 0, st);
+}

@@ -122,12 +122,14 @@ FUSED_CASES = [
 ]
 
 
+@pytest.mark.parametrize("entry", ["lcp_fused", "lcp_fused_ws"])
 @pytest.mark.parametrize("h,w,m,k,kind", FUSED_CASES)
-def test_fused_parity(lib, h, w, m, k, kind):
+def test_fused_parity(lib, h, w, m, k, kind, entry):
     d = _fields(h, w, m, seed=h + 3 * w, kind=kind, k=k) if kind == "fourier" else _fields(h, w, m, 0, kind)
     iso = d["isovalues"][:k] if len(d["isovalues"]) >= k else np.linspace(-0.5, 0.5, k).astype(np.float32)
     ddof = 1 if m > 1 else 0
-    lcp, mask = lib.lcp_fused(_dev(d["u"]), _dev(d["v"]), iso, d["dx"], d["dy"], ddof=ddof, mask=True)
+    fn = getattr(lib, entry)
+    lcp, mask = fn(_dev(d["u"]), _dev(d["v"]), iso, d["dx"], d["dy"], ddof=ddof, mask=True)
     ref = O.lcp_closed_form(d["u"], d["v"], d["dx"], d["dy"], iso, ddof)
     err = np.abs(_np(lcp) - ref["lcp"])
     assert np.max(err) <= LCP_TOL, np.max(err)
@@ -147,54 +149,60 @@ def test_fused_equals_unfused_chain(lib):
     assert torch.max(torch.abs(fused - chain)).item() <= 2e-6
 
 
-def test_fused_fp16_output_within_one_ulp(lib):
+@pytest.mark.parametrize("entry", ["lcp_fused", "lcp_fused_ws"])
+def test_fused_fp16_output_within_one_ulp(lib, entry):
     d = _fields(61, 256, 10, seed=9, k=4)
-    lcp, _ = lib.lcp_fused(_dev(d["u"]), _dev(d["v"]), d["isovalues"], out_dtype=torch.float16)
+    lcp, _ = getattr(lib, entry)(_dev(d["u"]), _dev(d["v"]), d["isovalues"], out_dtype=torch.float16)
     ref = O.lcp_closed_form(d["u"], d["v"], 1.0, 1.0, d["isovalues"])["lcp"]
     ref16 = ref.astype(np.float16).astype(np.float64)
     ulp = np.spacing(np.abs(ref16).astype(np.float16)).astype(np.float64)
     assert np.all(np.abs(_np(lcp) - ref16) <= ulp + 1e-12)
 
 
-def test_fused_bf16_members(lib):
+@pytest.mark.parametrize("entry", ["lcp_fused", "lcp_fused_ws"])
+def test_fused_bf16_members(lib, entry):
+    fn = getattr(lib, entry)
     d = _fields(64, 512, 20, seed=11, k=4)
     u16, v16 = _dev(d["u"], torch.bfloat16), _dev(d["v"], torch.bfloat16)
-    lcp, _ = lib.lcp_fused(u16, v16, d["isovalues"])
+    lcp, _ = fn(u16, v16, d["isovalues"])
     ref = O.lcp_closed_form(_np(u16), _np(v16), 1.0, 1.0, d["isovalues"])["lcp"]  # same bf16-rounded values
     assert np.max(np.abs(_np(lcp) - ref)) <= LCP_TOL
     # odd width: scalar bf16 path
     d = _fields(33, 99, 5, seed=12, k=2)
     u16, v16 = _dev(d["u"], torch.bfloat16), _dev(d["v"], torch.bfloat16)
-    lcp, _ = lib.lcp_fused(u16, v16, d["isovalues"])
+    lcp, _ = fn(u16, v16, d["isovalues"])
     ref = O.lcp_closed_form(_np(u16), _np(v16), 1.0, 1.0, d["isovalues"])["lcp"]
     assert np.max(np.abs(_np(lcp) - ref)) <= LCP_TOL
 
 
-def test_fused_large_offset_keeps_accuracy(lib):
+@pytest.mark.parametrize("entry", ["lcp_fused", "lcp_fused_ws"])
+def test_fused_large_offset_keeps_accuracy(lib, entry):
     """|mean| / sigma ~ 2e5: the member-0 shift cancels the offset exactly."""
     d = _fields(48, 128, 20, seed=13, k=3)
     u = (d["u"] * 0.05 + 1e4).astype(np.float32)
     v = (d["v"] * 0.05 + 1e4).astype(np.float32)
     iso = (d["isovalues"] * 0.05).astype(np.float32)
-    lcp, _ = lib.lcp_fused(_dev(u), _dev(v), iso)
+    lcp, _ = getattr(lib, entry)(_dev(u), _dev(v), iso)
     ref = O.lcp_closed_form(u, v, 1.0, 1.0, iso)["lcp"]
     assert np.max(np.abs(_np(lcp) - ref)) <= LCP_TOL
 
 
-def test_fused_dyadic_zero_variance_is_bit_exact(lib):
+@pytest.mark.parametrize("entry", ["lcp_fused", "lcp_fused_ws"])
+def test_fused_dyadic_zero_variance_is_bit_exact(lib, entry):
     for (h, w, dx) in ((33, 68, 1.0), (20, 77, 0.5)):
         d = synth.dyadic_ensemble(h * w, h, w, m=4, k=3)
-        lcp, mask = lib.lcp_fused(_dev(d["u"]), _dev(d["v"]), d["isovalues"], dx, dx, mask=True)
+        lcp, mask = getattr(lib, entry)(_dev(d["u"]), _dev(d["v"]), d["isovalues"], dx, dx, mask=True)
         ref = O.lcp_closed_form(d["u"], d["v"], dx, dx, d["isovalues"])
         assert np.array_equal(lib.unpack_mask(mask, w).cpu().numpy(), ref["mask"])
         assert np.array_equal(_np(lcp), ref["lcp"])  # var = 0: LCP is the mask exactly
 
 
-def test_fused_nan_member_propagates(lib):
+@pytest.mark.parametrize("entry", ["lcp_fused", "lcp_fused_ws"])
+def test_fused_nan_member_propagates(lib, entry):
     d = _fields(20, 40, 6, seed=14, k=2)
     u = d["u"].copy()
     u[3, 10, 17] = np.nan
-    lcp, _ = lib.lcp_fused(_dev(u), _dev(d["v"]), d["isovalues"])
+    lcp, _ = getattr(lib, entry)(_dev(u), _dev(d["v"]), d["isovalues"])
     ref = O.lcp_closed_form(u, d["v"], 1.0, 1.0, d["isovalues"])["lcp"]
     got = _np(lcp)
     assert np.array_equal(np.isnan(got), np.isnan(ref)) and np.isnan(ref).any()
@@ -203,12 +211,13 @@ def test_fused_nan_member_propagates(lib):
 
 
 @pytest.mark.slow
-def test_fused_full_size_latlon(lib):
+@pytest.mark.parametrize("entry", ["lcp_fused", "lcp_fused_ws"])
+def test_fused_full_size_latlon(lib, entry):
     """The 721 x 1440 x 51, K = 8 workload in the bench's launch configuration,
     compared with the oracle on every cell."""
     d = synth.fourier_ensemble(0)
     u, v = _dev(d["u"]), _dev(d["v"])
-    lcp, mask = lib.lcp_fused(u, v, d["isovalues"], mask=True)
+    lcp, mask = getattr(lib, entry)(u, v, d["isovalues"], mask=True)
     ref = O.lcp_closed_form(d["u"], d["v"], 1.0, 1.0, d["isovalues"])
     assert np.max(np.abs(_np(lcp) - ref["lcp"])) <= LCP_TOL
     guard = _oracle_mask_guard(ref["mu_d"], d["isovalues"])
@@ -309,3 +318,58 @@ def test_register_streaming_variant_matches_oracle(tmp_path):
 def test_device_status_clear_after_runs(lib):
     torch.cuda.synchronize()
     assert lib.lcp_device_status() == 0
+
+
+def test_fused_ws_rejects_small_workspace(lib):
+    d = _fields(20, 64, 4, seed=15, k=2)
+    need = lib.lcp_fused_workspace_bytes(4, 20, 64)
+    ws = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lib.LcpError) as e:
+        lib.lcp_fused_ws(_dev(d["u"]), _dev(d["v"]), d["isovalues"], workspace=ws)
+    assert e.value.status == -1
+
+
+def test_fused_ws_repeated_calls_reuse_workspace(lib):
+    """Counters are reset by every call: back-to-back calls on one workspace agree."""
+    d = _fields(50, 300, 9, seed=16, k=3)
+    u, v = _dev(d["u"]), _dev(d["v"])
+    a, _ = lib.lcp_fused_ws(u, v, d["isovalues"])
+    b, _ = lib.lcp_fused_ws(u, v, d["isovalues"])
+    c, _ = lib.lcp_fused_ws(u, v, d["isovalues"][:2])
+    assert torch.equal(a, b) and torch.equal(a[:2], c)
+    assert lib.lcp_device_status() == 0
+
+
+def test_map_single_gaussian_vertex_tracks_the_normal_tail(lib):
+    """Cells with three deterministic vertices below c and one Gaussian vertex:
+    LCP = P(D >= c) = erfc((c - mu)/(sigma sqrt 2))/2 exactly, so this pins the
+    kernels' erfc over z in [-9, 9] against the oracle's FP64 erfc."""
+    n = 2001
+    z = np.linspace(-9.0, 9.0, n)
+    w = 2 * n + 1
+    mu = np.full((2, w), -1e3, np.float32)
+    var = np.zeros((2, w), np.float32)
+    sd = 0.37
+    mu[1, 1::2] = (-z * sd).astype(np.float32)  # c = 0: (c - mu)/sd = z
+    var[1, 1::2] = sd * sd
+    lcp, _ = lib.lcp_map(_dev(mu), _dev(var), [0.0])
+    ref = O.level_crossing_probability(mu, var, [0.0])
+    err = np.abs(_np(lcp) - ref)
+    assert err.max() <= 3e-7, err.max()
+
+
+def test_fused_ws_row_bands_match_oracle(lib):
+    """A grid of >= 2^18 vertices runs in bands of rows (48-row bands here), one
+    halo row each side, alternating two workspace buffers, each band's cells
+    on the auxiliary stream beside the next band's statistics."""
+    h, w, m = 250, 16384, 3
+    rng = np.random.default_rng(17)
+    base = np.cumsum(rng.normal(size=(h, w)) * 0.05, axis=1).astype(np.float32)
+    u = (base[None] + 0.3 * rng.standard_normal((m, h, w))).astype(np.float32)
+    v = (base[None] * 0.5 + 0.3 * rng.standard_normal((m, h, w))).astype(np.float32)
+    iso = np.array([-0.05, 0.02], np.float32)
+    lcp, mask = lib.lcp_fused_ws(_dev(u), _dev(v), iso, mask=True)
+    ref = O.lcp_closed_form(u, v, 1.0, 1.0, iso)
+    assert np.max(np.abs(_np(lcp) - ref["lcp"])) <= LCP_TOL
+    guard = _oracle_mask_guard(ref["mu_d"], iso)
+    assert np.array_equal(lib.unpack_mask(mask, w).cpu().numpy()[guard], ref["mask"][guard])
