@@ -134,17 +134,20 @@ def measured_hbm_peak():
 
 
 def profiled_traffic():
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    valid only while fused.cu is byte-identical to the source that was profiled."""
-    src = os.path.join(ROOT, "paper_2510_01190_gb300", "csrc", "fused.cu")
+    """DRAM bytes per step of the fused path (statistics + LCP kernels) from the
+    committed ncu summary, valid only while fused_ws.cu and lcp_common.cuh are
+    byte-identical to the sources that were profiled."""
+    csrc = os.path.join(ROOT, "paper_2510_01190_gb300", "csrc")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        txt = open(os.path.join(ROOT, "profiles", "lcp_fused_latlon_721x1440_m51_k8.md")).read()
+        h = hashlib.sha256()
+        for f in ("fused_ws.cu", "lcp_common.cuh"):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+        txt = open(os.path.join(ROOT, "profiles", "lcp_fused_ws_latlon_721x1440_m51_k8.md")).read()
     except OSError:
         return None
-    m_t = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", txt)
-    m_s = re.search(r"fused_cu_sha256:\s*([0-9a-f]{64})", txt)
-    if not m_t or not m_s or m_s.group(1) != sha:
+    m_t = re.search(r"traffic_bytes_per_step:\s*([0-9]+)", txt)
+    m_s = re.search(r"sources_sha256:\s*([0-9a-f]{64})", txt)
+    if not m_t or not m_s or m_s.group(1) != h.hexdigest():
         return None
     return int(m_t.group(1))
 
@@ -271,10 +274,8 @@ def our_arm(args):
     mask = torch.empty((K, Hc, lib.mask_words_per_row(W)), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    entry = lib.lcp_fused_ws if os.environ.get("LCP_BENCH_ENTRY", "ws") == "ws" else lib.lcp_fused
-
     def step():
-        entry(u, v, iso, 1.0, 1.0, 1, mask=True, out=out, mask_out=mask)
+        lib.lcp_fused_ws(u, v, iso, 1.0, 1.0, 1, mask=True, out=out, mask_out=mask)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -314,7 +315,7 @@ def our_arm(args):
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": profiled_traffic(), "peak_kind": peak_kind,
-            "kernel": "lcp_fused_ws: stats_ws_kernel<float,4> + lcp_rows_kernel<float>", "alg_bytes_per_launch": alg_bytes,
+            "kernel": "lcp_fused_ws step: stats_ws_kernel<float,4> + lcp_rows_kernel<8,mask,float>", "alg_bytes_per_launch": alg_bytes,
             "kernel_ms": round(kern_ms, 5)}
 
     # end to end through the host-buffer API: pinned members in, LCP + mask out
@@ -356,7 +357,7 @@ def our_arm(args):
                        "l2": "no flush: inputs 424 MB > 129 MB L2",
                        "lcp_values_per_s": value * K, "hbm_frac_of_measured": roof["frac"]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "vs_mc": vs_mc,
-            "clocks": clk, "gpu_launches": n,
+            "clocks": clk, "gpu_launches": 2 * n,  # statistics + LCP kernel per step (the counter reset is a memset)
             "gpu": torch.cuda.get_device_name(dev),
         }
         print(json.dumps(line), flush=True)

@@ -288,6 +288,20 @@ __device__ __forceinline__ float2 vertex_pq(float mu, float s, bool zero, float 
     return make_float2(pos ? e : 1.0f - e, pos ? 1.0f - e : e);
 }
 
+// vertex_pq for two isovalues (c.x, c.y) of one vertex, paired erfc.
+__device__ __forceinline__ void vertex_pq2(float mu, float s, bool zero, float2 c, bool below0, bool below1,
+                                           float2& pq0, float2& pq1) {
+    float2 t = __fmul2_rn(__fadd2_rn(make_float2(mu, mu), make_float2(-c.x, -c.y)), make_float2(s, s));
+    if (zero) {
+        t.x = below0 ? -1.0e4f : 1.0e4f;
+        t.y = below1 ? -1.0e4f : 1.0e4f;
+    }
+    const float2 e = half_erfc_nonneg2(make_float2(fabsf(t.x), fabsf(t.y)));
+    const bool pos0 = t.x >= 0.0f, pos1 = t.y >= 0.0f;
+    pq0 = make_float2(pos0 ? e.x : 1.0f - e.x, pos0 ? 1.0f - e.x : e.x);
+    pq1 = make_float2(pos1 ? e.y : 1.0f - e.y, pos1 ? 1.0f - e.y : e.y);
+}
+
 // Clamp to [0, 1] with NaN propagated (max.NaN / min.NaN).
 __device__ __forceinline__ float clamp01_nan(float x) {
     float r;
@@ -300,7 +314,7 @@ __device__ __forceinline__ float clamp01_nan(float x) {
 // isovalues exactly (other counts run as sums of such passes); MASK selects the
 // mean-field bits.
 template <int KX, bool MASK, typename OutT>
-__global__ void __launch_bounds__(kRT, KX <= 8 ? 3 : (KX <= 16 ? 2 : 1))
+__global__ void __launch_bounds__(kRT, KX <= 4 ? 3 : (KX <= 16 ? 2 : 1))
     lcp_rows_kernel(const __grid_constant__ RowsParams p, const __grid_constant__ IsoParams iso) {
     constexpr int NV = kRT + 1;                      // vertices per tile row
     extern __shared__ __align__(16) float2 pq[];     // [KX][NV] (P(D < c), P(D >= c)) of the current row
@@ -390,11 +404,20 @@ __global__ void __launch_bounds__(kRT, KX <= 8 ? 3 : (KX <= 16 ? 2 : 1))
             const bool zero = var == 0.0f;
             const float s = rsqrtf(2.0f * var);
             uint32_t b = 0;
+            if constexpr (KX == 1) {
+                const bool below = mu < c[0];
+                pq[t] = vertex_pq(mu, s, zero, c[0], below);
+                b = below;
+            } else {
 #pragma unroll
-            for (int k = 0; k < KX; ++k) {
-                const bool below = mu < c[k];
-                pq[k * NV + t] = vertex_pq(mu, s, zero, c[k], below);
-                b |= (uint32_t)below << k;
+                for (int k = 0; k < KX; k += 2) {
+                    const bool below0 = mu < c[k], below1 = mu < c[k + 1];
+                    float2 a0, a1;
+                    vertex_pq2(mu, s, zero, make_float2(c[k], c[k + 1]), below0, below1, a0, a1);
+                    pq[k * NV + t] = a0;
+                    pq[(k + 1) * NV + t] = a1;
+                    b |= ((uint32_t)below0 << k) | ((uint32_t)below1 << (k + 1));
+                }
             }
             cls[t] = b;
         }
@@ -423,8 +446,8 @@ __global__ void __launch_bounds__(kRT, KX <= 8 ? 3 : (KX <= 16 ? 2 : 1))
             uint32_t* m = pm;
 #pragma unroll
             for (int k = 0; k < KX; ++k) {
-                const float2 v0 = pq[k * NV + t], v1 = pq[k * NV + t + 1];
-                const float ph = v0.x * v1.x, qh = v0.y * v1.y;
+                const float2 h = __fmul2_rn(pq[k * NV + t], pq[k * NV + t + 1]);  // (p_i p_i+1, q_i q_i+1)
+                const float ph = h.x, qh = h.y;
                 const float lcp = fmaf(-qh_prev[k], qh, fmaf(-ph_prev[k], ph, 1.0f));
                 if (ok) *o = to_out<OutT>(clamp01_nan(lcp));
                 o += plane;

@@ -134,6 +134,27 @@ __device__ __forceinline__ float half_erfc_nonneg(float x) {
     return t * ex2_approx(fmaf(-x * L, x, r));
 }
 
+// Two evaluations of half_erfc_nonneg at once with Blackwell's paired FP32
+// instructions (FFMA2 / FMUL2 on float2): the same polynomial and constants,
+// half the FMA-pipe instructions; the reciprocals and exponentials stay scalar.
+__device__ __forceinline__ float2 half_erfc_nonneg2(float2 x) {
+    constexpr float L = 1.4426950408889634f;  // log2(e)
+    const float2 den = __ffma2_rn(make_float2(0.5f, 0.5f), x, make_float2(1.0f, 1.0f));
+    const float2 t = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+    float2 r = make_float2(0.17087277f * L, 0.17087277f * L);
+    r = __ffma2_rn(r, t, make_float2(-0.82215223f * L, -0.82215223f * L));
+    r = __ffma2_rn(r, t, make_float2(1.48851587f * L, 1.48851587f * L));
+    r = __ffma2_rn(r, t, make_float2(-1.13520398f * L, -1.13520398f * L));
+    r = __ffma2_rn(r, t, make_float2(0.27886807f * L, 0.27886807f * L));
+    r = __ffma2_rn(r, t, make_float2(-0.18628806f * L, -0.18628806f * L));
+    r = __ffma2_rn(r, t, make_float2(0.09678418f * L, 0.09678418f * L));
+    r = __ffma2_rn(r, t, make_float2(0.37409196f * L, 0.37409196f * L));
+    r = __ffma2_rn(r, t, make_float2(1.00002368f * L, 1.00002368f * L));
+    r = __ffma2_rn(r, t, make_float2(-1.95865941f * L, -1.95865941f * L));
+    const float2 ex = __ffma2_rn(__fmul2_rn(x, make_float2(-L, -L)), x, r);
+    return __fmul2_rn(t, make_float2(ex2_approx(ex.x), ex2_approx(ex.y)));
+}
+
 // Per-vertex part of (p, q): s = 1 / (sigma sqrt 2), or s = 0 marks var == 0.
 struct VertexG {
     float mu, s;
