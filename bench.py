@@ -53,6 +53,24 @@ def parse():
 
 
 # ---------------------------------------------------------------------------
+def max_over_ranks(ms: float, device=None) -> float:
+    """Max of a per-rank duration over the process group (the job's time); the
+    value itself when no group is initialised or the world is one rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(cells_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank processes its own field of `cells_per_rank` cells."""
+    return world * cells_per_rank / (max_ms / 1e3)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -301,12 +319,9 @@ def our_arm(args):
     clocks.stop()
     total_ms = ev[0][0].elapsed_time(ev[-1][1])
     kern_ms = sum(a.elapsed_time(b) for a, b in ev) / n
-    if pg:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(total_ms, device=dev)
     ms_per_step = total_ms / n
-    value = world * Hc * Wc / (ms_per_step / 1e3)
+    value = weak_scaling_value(Hc * Wc, world, ms_per_step)
 
     # algorithmic bytes of one launch: members read once + LCP map + mask written once
     n_words = lib.mask_words_per_row(W)
