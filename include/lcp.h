@@ -157,6 +157,27 @@ lcp_status lcp_fused_ws(const void* u, const void* v, lcp_dtype in_dtype, int M,
                         size_t workspace_bytes, lcp_stream_t stream);
 
 /*
+ * lcp_fused_static_ws - lcp_fused_ws with its scratch in a 64 MiB file-scope
+ * device array of the library instead of a caller workspace, so that the call
+ * allocates no memory: for callers that hold no device allocator, or that must
+ * not pay an allocation's device synchronisation (or its failure under memory
+ * pressure) inside a steady-state loop.  The paper has no counterpart: it is a
+ * host-interface convenience around the same computation (Eqs. 1-3 and the LCP
+ * of Sec. 3.2), with the same arguments and results as lcp_fused_ws.
+ * Set-up: the first call on each device (with that device current) looks up
+ * the array's device address; make that first call before any stream capture.
+ * The per-band counters that must start at zero are cleared on `stream` by
+ * every call.  The one array is shared by all calls on a device: calls that
+ * overlap in time (other streams, other host threads) race and give undefined
+ * results.  Errors: LCP_ERR_ARG when lcp_fused_workspace_bytes(M, H, W,
+ * in_dtype) exceeds 64 MiB (grids wider than about 190,000 vertices) or on any
+ * argument lcp_fused_ws rejects; LCP_ERR_CUDA when the address lookup fails.
+ */
+lcp_status lcp_fused_static_ws(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
+                               int64_t member_stride, int ddof, double dx, double dy, const float* iso, int K,
+                               void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, lcp_stream_t stream);
+
+/*
  * lcp_mc - classical Monte Carlo estimate of the LCP map (Sec. 3.2 and Sec. 4):
  * every sample is one realisation of the whole field; its divergence (Eq. 1,
  * same boundary rule) is tested per cell and isovalue, "crossing" meaning

@@ -24,6 +24,7 @@ __all__ = [
     "lcp_map",
     "lcp_fused",
     "lcp_fused_ws",
+    "lcp_fused_static_ws",
     "lcp_fused_workspace_bytes",
     "lcp_fused_host",
     "lcp_mc",
@@ -64,6 +65,8 @@ _SIGNATURES = {
     "lcp_fused_workspace_bytes": (ctypes.c_size_t, [c_int, c_int, c_int, c_int]),
     "lcp_fused_ws": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double, c_fp, c_int,
                              c_vp, c_int, c_vp, c_vp, ctypes.c_size_t, c_vp]),
+    "lcp_fused_static_ws": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double, c_fp,
+                                    c_int, c_vp, c_int, c_vp, c_vp]),
 }
 
 
@@ -244,6 +247,21 @@ def lcp_fused_ws(u, v, isovalues, dx: float = 1.0, dy: float = 1.0, ddof: int = 
     _check(lib.lcp_fused_ws(_ptr(u), _ptr(v), _dtype_code(u.dtype), m, h, w, stride, ddof, float(dx), float(dy),
                             iso_p, k, _ptr(out), _dtype_code(out.dtype), _ptr(mask_out), c_vp(ws_ptr), ws_bytes,
                             _stream()))
+    return out, mask_out
+
+
+def lcp_fused_static_ws(u, v, isovalues, dx: float = 1.0, dy: float = 1.0, ddof: int = 1, out_dtype=torch.float32,
+                        mask: bool = False, out=None, mask_out=None):
+    """``lcp_fused_ws`` with the library's fixed 64 MiB device scratch: the C
+    call allocates nothing (pass ``out``/``mask_out`` to keep this wrapper from
+    allocating them).  Calls on one device must not overlap in time.
+    Returns (lcp, mask_words|None)."""
+    m, h, w, stride = _members(u, v)
+    iso, k, iso_p = _iso(isovalues)
+    out, mask_out = _outputs(k, h, w, u.device, out_dtype, mask, out, mask_out)
+    _check(load().lcp_fused_static_ws(_ptr(u), _ptr(v), _dtype_code(u.dtype), m, h, w, stride, ddof, float(dx),
+                                      float(dy), iso_p, k, _ptr(out), _dtype_code(out.dtype), _ptr(mask_out),
+                                      _stream()))
     return out, mask_out
 
 

@@ -1,0 +1,62 @@
+"""lcp_fused_static_ws, the entry point that allocates nothing (its scratch is a
+fixed device array of the library), called through the C ABI: two calls in a
+row must each agree with lcp_fused_ws on its own workspace.  Collected last so
+that it also runs after every other test in one process."""
+
+import ctypes
+
+import pytest
+import torch
+
+from paper_2510_01190_gb300 import synth
+
+LCP_TOL = 1e-5
+
+CASES = [
+    # (h, w, m, k, member dtype)
+    (97, 203, 9, 5, torch.float32),
+    (64, 130, 12, 3, torch.bfloat16),
+    (721, 1440, 51, 8, torch.float32),
+]
+
+
+def _call_static(clib, u, v, iso, out, mask):
+    m, h, w = u.shape
+    code = {torch.float32: 0, torch.bfloat16: 1}[u.dtype]
+    iso_c = (ctypes.c_float * len(iso))(*[float(c) for c in iso])
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return clib.lcp_fused_static_ws(ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(v.data_ptr()), code, m, h, w,
+                                    h * w, 1, 1.0, 1.0, iso_c, len(iso), ctypes.c_void_p(out.data_ptr()), 0,
+                                    ctypes.c_void_p(mask.data_ptr()), stream)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("h,w,m,k,dt", CASES)
+def test_static_scratch_matches_workspace_path_twice(lib, h, w, m, k, dt):
+    f = synth.fourier_ensemble(seed=11, h=h, w=w, m=m, k=k)
+    u = torch.from_numpy(f["u"]).cuda().to(dt).contiguous()
+    v = torch.from_numpy(f["v"]).cuda().to(dt).contiguous()
+    iso = f["isovalues"]
+    ref, ref_mask = lib.lcp_fused_ws(u, v, iso, 1.0, 1.0, 1, mask=True)
+    clib = lib.load()
+    nw = lib.mask_words_per_row(w)
+    for _ in range(2):
+        out = torch.full((k, h - 1, w - 1), float("nan"), device="cuda")
+        mask = torch.full((k, h - 1, nw), -1, dtype=torch.int32, device="cuda")
+        assert _call_static(clib, u, v, iso, out, mask) == 0, clib.lcp_last_error()
+        torch.cuda.synchronize()
+        err = (out - ref).abs().max().item()
+        assert err <= LCP_TOL, err
+        assert torch.equal(mask, ref_mask)
+    assert lib.lcp_device_status(reset=True) == 0
+
+
+@pytest.mark.gpu
+def test_static_scratch_rejects_grids_above_its_maximum(lib):
+    clib = lib.load()
+    iso_c = (ctypes.c_float * 1)(0.0)
+    # 100 x 400000 needs about 140 MB of scratch, more than the 64 MiB array
+    s = clib.lcp_fused_static_ws(None, None, 0, 2, 100, 400000, 100 * 400000, 1, 1.0, 1.0, iso_c, 1, None, 0, None,
+                                 None)
+    assert s == -1
+    assert b"static maximum" in clib.lcp_last_error()
