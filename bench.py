@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-mc", action="store_true", help="skip the Monte Carlo equal-error comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--workload", choices=["latlon", "batch"], default="latlon",
+                    help="latlon: the 721x1440 field (default); batch: 256 uneven fields in one persistent launch")
+    ap.add_argument("--tile", type=str, default=None,
+                    help="batch workload: force the tile shape ROWS,COLS instead of autotuning")
+    ap.add_argument("--fields", type=int, default=256,
+                    help="batch workload: use the first N of its 256 field descriptors (small cases for profiling)")
     return ap.parse_args()
 
 
@@ -151,16 +157,15 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic():
-    """DRAM bytes per step of the fused path (statistics + LCP kernels) from the
-    committed ncu summary, valid only while fused_ws.cu and lcp_common.cuh are
-    byte-identical to the sources that were profiled."""
+def profiled_traffic(profile="lcp_fused_ws_latlon_721x1440_m51_k8.md", sources=("fused_ws.cu", "lcp_common.cuh")):
+    """DRAM bytes per step of a kernel path from its committed ncu summary, valid
+    only while the listed sources are byte-identical to the ones profiled."""
     csrc = os.path.join(ROOT, "paper_2510_01190_gb300", "csrc")
     try:
         h = hashlib.sha256()
-        for f in ("fused_ws.cu", "lcp_common.cuh"):
+        for f in sources:
             h.update(open(os.path.join(csrc, f), "rb").read())
-        txt = open(os.path.join(ROOT, "profiles", "lcp_fused_ws_latlon_721x1440_m51_k8.md")).read()
+        txt = open(os.path.join(ROOT, "profiles", profile)).read()
     except OSError:
         return None
     m_t = re.search(r"traffic_bytes_per_step:\s*([0-9]+)", txt)
@@ -381,10 +386,129 @@ def our_arm(args):
     return 0
 
 
+BATCH_WORKLOAD = ("batch of 256 fields, H and W log-uniform in [128, 2048], 10-100 members fp32 (u,v), "
+                  "16 isovalues each, fp16 LCP maps; one persistent launch in a CUDA graph, autotuned tiles")
+
+
+def batch_cpu_baseline(fields, budget_s=12.0):
+    """The FP64 oracle, as it stands, on whole fields of the batch (smallest first) for ~budget_s."""
+    import oracle as O
+
+    order = np.argsort([f["u"].numel() for f in fields])
+    cells, n, t0 = 0, 0, time.perf_counter()
+    for i in order:
+        f = fields[i]
+        u, v = f["u"].cpu().numpy(), f["v"].cpu().numpy()
+        O.lcp_closed_form(u, v, 1.0, 1.0, f["isovalues"])
+        cells += (u.shape[1] - 1) * (u.shape[2] - 1)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the {n} smallest of the 256 fields whole, K=16 (FP64 numpy, single thread)",
+            "seconds": round(dt, 2)}
+
+
+def batch_arm(args):
+    """256 uneven fields per step, one persistent graph-captured launch; each rank its own batch."""
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = False
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = True
+    import paper_2510_01190_gb300 as lib
+    from paper_2510_01190_gb300 import synth
+
+    lib.load()
+    fields = synth.fourier_batch_torch(synth.batch_descriptors(0)[:max(1, args.fields)], k=16, device=dev)
+    b = lib.Batch(fields, out_dtype=torch.float16)
+    plan = b.plan
+    if args.tile:
+        best, tune_ms = tuple(int(x) for x in args.tile.split(",")), []
+    else:
+        best, tune_ms = b.autotune(reps=2)
+    stream = torch.cuda.Stream(device=dev)
+    b.run(best)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(graph, stream=stream):
+            b.run(best)
+    torch.cuda.synchronize()
+    for _ in range(max(args.warmup, 3)):
+        graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local).start()
+    time.sleep(0.35)
+    n = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    if pg:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    cur = torch.cuda.current_stream()
+    for i in range(n):
+        ev[i][0].record(cur)
+        graph.replay()
+        ev[i][1].record(cur)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if pg:
+        torch.distributed.barrier()
+    time.sleep(0.25)
+    clocks.stop()
+    total_ms = ev[0][0].elapsed_time(ev[-1][1])
+    kern_ms = sum(x.elapsed_time(y) for x, y in ev) / n
+    total_ms = max_over_ranks(total_ms, device=dev)
+    ms_per_step = total_ms / n
+    value = weak_scaling_value(plan.cells, world, ms_per_step)
+    alg = plan.member_bytes + plan.out_bytes
+    peak, peak_kind = measured_hbm_peak()
+    achieved = alg / (kern_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": profiled_traffic("lcp_batch_256fields_k16_f16.md", ("batch.cu", "lcp_common.cuh")),
+            "peak_kind": peak_kind, "kernel": f"batch_kernel<float,half,{best[0]},{best[1]}> (persistent)",
+            "alg_bytes_per_launch": alg, "kernel_ms": round(kern_ms, 4)}
+    cpu = batch_cpu_baseline(fields) if (not args.no_cpu and rank == 0 and world == 1) else None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD if plan.n_fields == 256 else
+                       f"first {plan.n_fields} fields of: " + BATCH_WORKLOAD, "fields": plan.n_fields, "cells": plan.cells,
+                       "cell_isovalues": plan.cell_isovalues, "member_bytes": plan.member_bytes,
+                       "out_bytes": plan.out_bytes, "tile": list(best), "autotune_ms": [round(x, 3) for x in tune_ms],
+                       "global_batch": world, "parallelism": f"independent batches x{world}" if world > 1 else "single",
+                       "l2": f"no flush: inputs {plan.member_bytes / 1e9:.1f} GB > 129 MB L2",
+                       "lcp_values_per_s": world * plan.cell_isovalues / (ms_per_step / 1e3),
+                       "hbm_frac_of_measured": roof["frac"]},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": None, "e2e_note": "not measured for the batch: its 59 GB of members would have to be pinned on the host",
+            "clocks": clocks.summary(t_wall0, t_wall1), "gpu_launches": n,  # one persistent kernel per step
+            "gpu": torch.cuda.get_device_name(dev),
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "batch":
+        return batch_arm(args)
     return our_arm(args)
 
 

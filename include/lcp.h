@@ -178,6 +178,101 @@ lcp_status lcp_fused_static_ws(const void* u, const void* v, lcp_dtype in_dtype,
                                void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, lcp_stream_t stream);
 
 /*
+ * Batched closed form: many fields of uneven size (each its own H, W, M,
+ * spacing and isovalue list) evaluated by ONE persistent kernel launch.  The
+ * computation per field is exactly lcp_fused's (Eqs. 1-3 per vertex, the LCP of
+ * Sec. 3.2 per cell and isovalue, the mean-field mask); the paper evaluates one
+ * field at a time, and batching is this library's addition.
+ *
+ * lcp_field_desc - one field of a batch (all pointers are device pointers owned
+ * by the caller; they must stay valid for every lcp_batch call of the plan):
+ *   u, v            [M][H][W] members of the two components, row-major planes
+ *   member_stride   elements between consecutive members (>= H*W when M > 1)
+ *   M, H, W, ddof   members, vertex rows, vertex columns, variance ddof
+ *   dx, dy          grid spacing (finite, > 0)
+ *   iso_begin, K    the field's isovalues are iso[iso_begin .. iso_begin+K) of
+ *                   the batch's isovalue table
+ *   lcp_out         [K][H-1][W-1] of the plan's out_dtype
+ *   mask            [K][H-1][ceil((W-1)/32)] uint32 mean-field mask, or NULL
+ */
+typedef struct {
+    const void* u;
+    const void* v;
+    int64_t member_stride;
+    int M, H, W, ddof;
+    double dx, dy;
+    int iso_begin, K;
+    void* lcp_out;
+    uint32_t* mask;
+} lcp_field_desc;
+
+/*
+ * lcp_tune - launch shape of the batch kernel: a tile of tile_rows cell rows by
+ * tile_cols cell columns, one of (64, 64), (32, 128), (32, 64), (16, 128);
+ * ctas_per_sm = 0 takes as many CTAs per SM as fit.
+ */
+typedef struct {
+    int tile_rows, tile_cols;
+    int ctas_per_sm;
+} lcp_tune;
+
+/*
+ * lcp_batch_plan - filled by lcp_batch_prepare; read by lcp_batch and
+ * lcp_batch_autotune.  Plain data: copy it freely, do not edit it.
+ */
+typedef struct {
+    void* workspace;
+    size_t workspace_bytes;
+    int n_fields, n_iso;
+    lcp_dtype in_dtype, out_dtype;
+    int64_t cells;            /* sum over fields of (H-1)(W-1) */
+    int64_t cell_isovalues;   /* sum over fields of K (H-1)(W-1) */
+    int64_t member_bytes;     /* bytes of u and v read once */
+    int64_t out_bytes;        /* bytes of LCP maps and masks written once */
+} lcp_batch_plan;
+
+/* Device workspace a batch of n_fields fields and n_iso isovalues needs. */
+size_t lcp_batch_workspace_bytes(int n_fields, int n_iso);
+
+/*
+ * lcp_batch_prepare - validate every descriptor on the host (the checks of
+ * lcp_fused, per field, with 1 <= K <= LCP_MAX_ISOVALUES and iso_begin + K <=
+ * n_iso) and write the batch's work
+ * table (field records ordered by cost, tile prefix sums for every tile shape,
+ * the isovalue table) into `workspace` (device, 256-byte aligned, at least
+ * lcp_batch_workspace_bytes).  fields and iso are HOST arrays and may be freed
+ * on return: the call copies them on `stream` and synchronises with it, so it
+ * must not be called during stream capture.  in_dtype LCP_F32 or LCP_BF16;
+ * out_dtype LCP_F32 or LCP_F16.  Errors: LCP_ERR_ARG naming the first bad
+ * field; LCP_ERR_CUDA.
+ */
+lcp_status lcp_batch_prepare(const lcp_field_desc* fields, int n_fields, const float* iso, int n_iso,
+                             lcp_dtype in_dtype, lcp_dtype out_dtype, void* workspace, size_t workspace_bytes,
+                             lcp_stream_t stream, lcp_batch_plan* plan);
+
+/*
+ * lcp_batch - evaluate every field of a prepared plan: a memset node (the tile
+ * counter) and one persistent kernel launch on `stream`, nothing else, so the
+ * call can be captured into a CUDA graph once it has run outside capture on the
+ * device (the first call sets the kernel's shared-memory limit).  tune == NULL
+ * takes (64, 64).  Each CTA takes tiles from the batch's work list in turn and
+ * computes a tile's statistics and its one-vertex halo itself, so no CTA waits
+ * on another.  Calls sharing one workspace must not overlap in time.  Errors:
+ * LCP_ERR_ARG for an unknown tile shape or an unprepared plan; LCP_ERR_CUDA.
+ */
+lcp_status lcp_batch(const lcp_batch_plan* plan, const lcp_tune* tune, lcp_stream_t stream);
+
+/*
+ * lcp_batch_autotune - time every tile shape of lcp_tune (reps runs each, CUDA
+ * events on `stream`, after one warm-up run) on the plan itself and return the
+ * fastest in *best; ms (optional, HOST, 4 floats) receives each shape's mean
+ * time in the order listed under lcp_tune.  Writes the plan's outputs (with the
+ * correct results).  Synchronises; not for use during stream capture.
+ */
+lcp_status lcp_batch_autotune(const lcp_batch_plan* plan, int reps, lcp_tune* best, float* ms,
+                              lcp_stream_t stream);
+
+/*
  * lcp_mc - classical Monte Carlo estimate of the LCP map (Sec. 3.2 and Sec. 4):
  * every sample is one realisation of the whole field; its divergence (Eq. 1,
  * same boundary rule) is tested per cell and isovalue, "crossing" meaning

@@ -27,6 +27,15 @@ __all__ = [
     "lcp_fused_static_ws",
     "lcp_fused_workspace_bytes",
     "lcp_fused_host",
+    "lcp_field_desc",
+    "lcp_tune",
+    "lcp_batch_plan",
+    "TILE_SHAPES",
+    "lcp_batch_workspace_bytes",
+    "lcp_batch_prepare",
+    "lcp_batch",
+    "lcp_batch_autotune",
+    "Batch",
     "lcp_mc",
     "lcp_philox_fill",
     "lcp_device_status",
@@ -49,6 +58,31 @@ _LOCK = threading.Lock()
 c_int, c_i64, c_u64, c_u32, c_double = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double
 c_vp, c_fp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)
 
+
+class lcp_field_desc(ctypes.Structure):
+    """One field of a batch (the C struct of the same name)."""
+
+    _fields_ = [("u", c_vp), ("v", c_vp), ("member_stride", c_i64), ("M", c_int), ("H", c_int), ("W", c_int),
+                ("ddof", c_int), ("dx", c_double), ("dy", c_double), ("iso_begin", c_int), ("K", c_int),
+                ("lcp_out", c_vp), ("mask", c_vp)]
+
+
+class lcp_tune(ctypes.Structure):
+    """Tile shape of the batch kernel (the C struct of the same name)."""
+
+    _fields_ = [("tile_rows", c_int), ("tile_cols", c_int), ("ctas_per_sm", c_int)]
+
+
+class lcp_batch_plan(ctypes.Structure):
+    """A prepared batch (the C struct of the same name)."""
+
+    _fields_ = [("workspace", c_vp), ("workspace_bytes", ctypes.c_size_t), ("n_fields", c_int), ("n_iso", c_int),
+                ("in_dtype", c_int), ("out_dtype", c_int), ("cells", c_i64), ("cell_isovalues", c_i64),
+                ("member_bytes", c_i64), ("out_bytes", c_i64)]
+
+
+TILE_SHAPES = [(64, 64), (32, 128), (32, 64), (16, 128)]
+
 _SIGNATURES = {
     "lcp_status_string": (ctypes.c_char_p, [c_int]),
     "lcp_last_error": (ctypes.c_char_p, []),
@@ -65,6 +99,11 @@ _SIGNATURES = {
     "lcp_fused_workspace_bytes": (ctypes.c_size_t, [c_int, c_int, c_int, c_int]),
     "lcp_fused_ws": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double, c_fp, c_int,
                              c_vp, c_int, c_vp, c_vp, ctypes.c_size_t, c_vp]),
+    "lcp_batch_workspace_bytes": (ctypes.c_size_t, [c_int, c_int]),
+    "lcp_batch_prepare": (c_int, [ctypes.POINTER(lcp_field_desc), c_int, c_fp, c_int, c_int, c_int, c_vp,
+                                  ctypes.c_size_t, c_vp, ctypes.POINTER(lcp_batch_plan)]),
+    "lcp_batch": (c_int, [ctypes.POINTER(lcp_batch_plan), ctypes.POINTER(lcp_tune), c_vp]),
+    "lcp_batch_autotune": (c_int, [ctypes.POINTER(lcp_batch_plan), c_int, ctypes.POINTER(lcp_tune), c_fp, c_vp]),
     "lcp_fused_static_ws": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double, c_fp,
                                     c_int, c_vp, c_int, c_vp, c_vp]),
 }
@@ -349,6 +388,85 @@ def lcp_device_status(reset: bool = False) -> int:
     if status not in (0, -4):
         _check(status)
     return int(flags.value)
+
+
+def lcp_batch_workspace_bytes(n_fields: int, n_iso: int) -> int:
+    return int(load().lcp_batch_workspace_bytes(n_fields, n_iso))
+
+
+def lcp_batch_prepare(descs, iso, in_dtype, out_dtype, workspace, stream=None) -> lcp_batch_plan:
+    """Validate a list of ``lcp_field_desc`` and write the work table into
+    ``workspace`` (a uint8 CUDA tensor); returns the plan.  Synchronising."""
+    arr = (lcp_field_desc * len(descs))(*descs)
+    iso_t = torch.as_tensor(iso, dtype=torch.float32).reshape(-1).contiguous().cpu()
+    plan = lcp_batch_plan()
+    off = (-workspace.data_ptr()) % 256
+    _check(load().lcp_batch_prepare(arr, len(descs), ctypes.cast(iso_t.data_ptr(), c_fp), iso_t.numel(),
+                                    _dtype_code(in_dtype), _dtype_code(out_dtype), c_vp(workspace.data_ptr() + off),
+                                    workspace.numel() - off, stream if stream is not None else _stream(),
+                                    ctypes.byref(plan)))
+    return plan
+
+
+def lcp_batch(plan: lcp_batch_plan, tune=None, stream=None):
+    """One persistent launch over every field of ``plan`` (``tune`` = (rows, cols) or lcp_tune)."""
+    t = None
+    if tune is not None:
+        t = tune if isinstance(tune, lcp_tune) else lcp_tune(int(tune[0]), int(tune[1]), 0)
+    _check(load().lcp_batch(ctypes.byref(plan), ctypes.byref(t) if t is not None else None,
+                            stream if stream is not None else _stream()))
+
+
+def lcp_batch_autotune(plan: lcp_batch_plan, reps: int = 3, stream=None):
+    """Time every tile shape on the plan; returns ((rows, cols), [ms per shape])."""
+    best = lcp_tune()
+    ms = (ctypes.c_float * len(TILE_SHAPES))()
+    _check(load().lcp_batch_autotune(ctypes.byref(plan), int(reps), ctypes.byref(best),
+                                     ctypes.cast(ms, c_fp), stream if stream is not None else _stream()))
+    return (best.tile_rows, best.tile_cols), [float(x) for x in ms]
+
+
+class Batch:
+    """Many fields evaluated by one persistent launch.
+
+    ``fields``: list of dict(u, v, isovalues[, dx, dy]) with u, v CUDA tensors
+    [M, H, W] of one dtype (fp32 or bf16).  Allocates each field's outputs
+    (``lcp[f]`` [K, H-1, W-1] of ``out_dtype``; ``mask[f]`` words or None) and
+    the device workspace, and prepares the plan.  ``run()`` is capturable into
+    a CUDA graph once it has run outside capture.
+    """
+
+    def __init__(self, fields, out_dtype=torch.float32, mask: bool = False, ddof: int = 1):
+        if not fields:
+            raise ValueError("a batch needs at least one field")
+        dt = fields[0]["u"].dtype
+        dev = fields[0]["u"].device
+        self.fields = fields
+        self.lcp, self.mask, descs, iso = [], [], [], []
+        for f in fields:
+            u, v = f["u"], f["v"]
+            if u.dtype != dt:
+                raise ValueError("all fields of a batch share one member dtype")
+            m, h, w, stride = _members(u, v)
+            k = len(f["isovalues"])
+            out = torch.empty((k, h - 1, w - 1), dtype=out_dtype, device=dev)
+            mw = torch.zeros((k, h - 1, mask_words_per_row(w)), dtype=torch.int32, device=dev) if mask else None
+            descs.append(lcp_field_desc(u.data_ptr(), v.data_ptr(), stride, m, h, w, ddof, float(f.get("dx", 1.0)),
+                                        float(f.get("dy", 1.0)), len(iso), k, out.data_ptr(),
+                                        mw.data_ptr() if mw is not None else None))
+            iso.extend(float(c) for c in f["isovalues"])
+            self.lcp.append(out)
+            self.mask.append(mw)
+        nbytes = lcp_batch_workspace_bytes(len(descs), len(iso))
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        self.plan = lcp_batch_prepare(descs, iso, dt, out_dtype, self.workspace)
+
+    def run(self, tune=None):
+        lcp_batch(self.plan, tune)
+        return self.lcp, self.mask
+
+    def autotune(self, reps: int = 3):
+        return lcp_batch_autotune(self.plan, reps)
 
 
 def unpack_mask(mask_words, w: int):

@@ -192,6 +192,39 @@ __device__ __forceinline__ void below_above(float mu, float var, float c, float&
     below_above(vertex_g(mu, var), c, p, q);
 }
 
+// (P(D < c), P(D >= c)) of a vertex (mu, s = 1/(sigma sqrt 2)); below = mu < c.
+// Zero variance takes the argument +-1e4, whose erfc underflows to 0, giving the
+// indicator [mu < c] (also when mu == c) without a separate branch.
+__device__ __forceinline__ float2 vertex_pq(float mu, float s, bool zero, float c, bool below) {
+    float t = (mu - c) * s;
+    if (zero) t = below ? -1.0e4f : 1.0e4f;
+    const float e = half_erfc_nonneg(fabsf(t));
+    const bool pos = t >= 0.0f;  // NaN: false, and both results stay NaN
+    return make_float2(pos ? e : 1.0f - e, pos ? 1.0f - e : e);
+}
+
+// vertex_pq for two isovalues (c.x, c.y) of one vertex, paired erfc.
+__device__ __forceinline__ void vertex_pq2(float mu, float s, bool zero, float2 c, bool below0, bool below1,
+                                           float2& pq0, float2& pq1) {
+    float2 t = __fmul2_rn(__fadd2_rn(make_float2(mu, mu), make_float2(-c.x, -c.y)), make_float2(s, s));
+    if (zero) {
+        t.x = below0 ? -1.0e4f : 1.0e4f;
+        t.y = below1 ? -1.0e4f : 1.0e4f;
+    }
+    const float2 e = half_erfc_nonneg2(make_float2(fabsf(t.x), fabsf(t.y)));
+    const bool pos0 = t.x >= 0.0f, pos1 = t.y >= 0.0f;
+    pq0 = make_float2(pos0 ? e.x : 1.0f - e.x, pos0 ? 1.0f - e.x : e.x);
+    pq1 = make_float2(pos1 ? e.y : 1.0f - e.y, pos1 ? 1.0f - e.y : e.y);
+}
+
+// Clamp to [0, 1] with NaN propagated (max.NaN / min.NaN).
+__device__ __forceinline__ float clamp01_nan(float x) {
+    float r;
+    asm("max.NaN.f32 %0, %1, 0f00000000;" : "=f"(r) : "f"(x));
+    asm("min.NaN.f32 %0, %0, 0f3F800000;" : "+f"(r));
+    return r;
+}
+
 // Clamp to [0, 1] without turning NaN into a number.
 __device__ __forceinline__ float clamp01(float x) {
     if (x < 0.0f) x = 0.0f;

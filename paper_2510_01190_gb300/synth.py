@@ -37,6 +37,7 @@ __all__ = [
     "dyadic_ensemble",
     "random_stats",
     "batch_descriptors",
+    "fourier_batch_torch",
 ]
 
 
@@ -305,3 +306,60 @@ def batch_descriptors(seed: int = 0, n_fields: int = 256, hw_min: int = 128, hw_
         m = int(g.integers(m_min, m_max + 1))
         out.append(dict(h=h, w=w, m=m, seed=int(seed) * 100003 + f))
     return out
+
+
+def _fourier_component_torch(g, h, w, n_modes, kmax, device):
+    """``_fourier_component`` with the inverse FFTs on a torch device: the same
+    random wavevectors, amplitudes and phases drawn from ``g``."""
+    import torch
+
+    kk = [(kx, ky) for kx in range(-kmax, kmax + 1) for ky in range(-kmax, kmax + 1)
+          if 0 < kx * kx + ky * ky <= kmax * kmax]
+    pick = g.choice(len(kk), size=n_modes, replace=False)
+    coef = np.zeros((3, h, w), np.complex128)  # field, d/dx, d/dy (only n_modes nonzero entries)
+    for p in pick:
+        kx, ky = kk[p]
+        a = (kx * kx + ky * ky) ** -0.75 * np.exp(1j * g.uniform(0, 2 * np.pi))
+        coef[0, ky % h, kx % w] += a
+        coef[1, ky % h, kx % w] += a * 1j * 2 * np.pi * kx / w
+        coef[2, ky % h, kx % w] += a * 1j * 2 * np.pi * ky / h
+    out = torch.fft.ifft2(torch.from_numpy(coef).to(device)).real * (h * w)
+    return out[0], out[1], out[2]
+
+
+def fourier_batch_torch(descs, k: int = 16, device="cuda", dtype=None, n_modes: int = 200, kmax: int = 30,
+                        rms: float = 10.0, noise_median: float = 0.5, noise_shape: float = 0.5):
+    """Fields of the batched workload, made on ``device``: for every descriptor
+    of ``batch_descriptors`` (h, w, m, seed) the lat-lon generator's recipe --
+    200 random Fourier modes per component (|k| <= 30, energy ~ k^-3, RMS 10),
+    log-normal per-vertex noise levels (median 0.5, shape 0.5), Gaussian member
+    noise -- and ``k`` isovalues at the 5th..95th percentiles of the field's
+    analytic mean divergence.
+
+    returns list of dict(u, v [m, h, w] torch tensors of ``dtype`` (default
+    float32); dx = dy = 1; isovalues float32 [k])
+    """
+    import torch
+
+    if dtype is None:
+        dtype = torch.float32
+    fields = []
+    for d in descs:
+        h, w, m, seed = d["h"], d["w"], d["m"], d["seed"]
+        g = _rng(seed, 2)
+        u0, dudx, _ = _fourier_component_torch(g, h, w, n_modes, kmax, device)
+        v0, _, dvdy = _fourier_component_torch(g, h, w, n_modes, kmax, device)
+        su = rms / torch.sqrt(torch.mean(u0 * u0))
+        sv = rms / torch.sqrt(torch.mean(v0 * v0))
+        bu, bv = (u0 * su).float(), (v0 * sv).float()
+        div = (dudx * su + dvdy * sv).cpu().numpy()
+        tg = torch.Generator(device=device)
+        tg.manual_seed(int(seed) * 1000003 + 3)
+        nu = noise_median * torch.exp(noise_shape * torch.randn((h, w), generator=tg, device=device))
+        nv = noise_median * torch.exp(noise_shape * torch.randn((h, w), generator=tg, device=device))
+        u = (bu + nu * torch.randn((m, h, w), generator=tg, device=device)).to(dtype)
+        v = (bv + nv * torch.randn((m, h, w), generator=tg, device=device)).to(dtype)
+        iso = np.percentile(div, np.linspace(5, 95, k)).astype(np.float32) if k > 1 else \
+            np.array([np.median(div)], np.float32)
+        fields.append(dict(u=u, v=v, dx=1.0, dy=1.0, isovalues=iso))
+    return fields
