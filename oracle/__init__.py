@@ -18,7 +18,13 @@ All functions are pinned by ``tests/test_oracle_pins.py`` against closed forms,
 the paper's Fig. 2 worked example, exact rational arithmetic, brute-force
 sampling with an independent random generator, and (for Philox4x32-10) an
 independent open-source implementation.  ``exact_empirical_lcp`` is pinned by
-brute-force enumeration on small ensembles.
+brute-force enumeration on small ensembles.  ``surrogate`` (moments,
+divergence cumulants, features, the network and Adam of the learned surrogate)
+is pinned by ``tests/test_oracle_surrogate.py``: exact rational moments, the
+divergence's exact distribution enumerated over every stencil combination,
+hand-evaluated networks, a finite-difference gradient check and Adam's
+first-step property.
 """
 
 from .lcp_oracle import *  # noqa: F401,F403
+from . import surrogate  # noqa: F401,E402

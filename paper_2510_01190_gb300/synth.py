@@ -38,6 +38,7 @@ __all__ = [
     "random_stats",
     "batch_descriptors",
     "fourier_batch_torch",
+    "mlp_init_params",
 ]
 
 
@@ -363,3 +364,21 @@ def fourier_batch_torch(descs, k: int = 16, device="cuda", dtype=None, n_modes: 
             np.array([np.median(div)], np.float32)
         fields.append(dict(u=u, v=v, dx=1.0, dy=1.0, isovalues=iso))
     return fields
+
+
+def mlp_init_params(seed: int = 0, n_in: int = 17, hidden: int = 64):
+    """Initial weights of the 17 -> 64 -> 64 -> 1 surrogate network: Glorot-
+    uniform matrices (bound sqrt(6 / (fan_in + fan_out))), zero biases.
+    Layout as the network is written, x @ W: W1 [17, 64], W2 [64, 64], w3 [64].
+
+    returns dict of float32 arrays (b3 a 0-d array)
+    """
+    g = _rng(seed, 9)
+
+    def glorot(a, b, shape):
+        lim = math.sqrt(6.0 / (a + b))
+        return g.uniform(-lim, lim, shape).astype(np.float32)
+
+    return dict(W1=glorot(n_in, hidden, (n_in, hidden)), b1=np.zeros(hidden, np.float32),
+                W2=glorot(hidden, hidden, (hidden, hidden)), b2=np.zeros(hidden, np.float32),
+                w3=glorot(hidden, 1, (hidden,)), b3=np.zeros((), np.float32))
