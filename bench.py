@@ -49,10 +49,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-mc", action="store_true", help="skip the Monte Carlo equal-error comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--workload", choices=["latlon", "batch"], default="latlon",
+    ap.add_argument("--workload", choices=["latlon", "batch", "learned"], default="latlon",
                     help="latlon: the 721x1440 field (default); batch: 256 uneven fields in one persistent launch")
     ap.add_argument("--tile", type=str, default=None,
                     help="batch workload: force the tile shape ROWS,COLS instead of autotuning")
+    ap.add_argument("--train-epochs", type=int, default=20, help="learned workload: training epochs (untimed)")
     ap.add_argument("--fields", type=int, default=256,
                     help="batch workload: use the first N of its 256 field descriptors (small cases for profiling)")
     return ap.parse_args()
@@ -503,12 +504,231 @@ def batch_arm(args):
     return 0
 
 
+LEARNED_WORKLOAD = ("non-Gaussian 1024x1024, 50 members fp32 (skew-normal or 2-Gaussian-mixture noise), 8 isovalues; "
+                    "learned surrogate: member moments + fused cumulant features and BF16 tensor-core network")
+
+
+def measured_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+def learned_cpu_baseline(d, budget_s=12.0, rows=33):
+    """The FP64 surrogate oracle (moments, cumulants, features, network) on row bands."""
+    from oracle import surrogate as SO
+    from paper_2510_01190_gb300 import synth
+
+    p = {k: np.asarray(v, np.float64) for k, v in synth.mlp_init_params(0).items()}
+    h, w = d["u"].shape[1:]
+    cells, n, t0 = 0, 0, time.perf_counter()
+    while True:
+        j0 = (n * 97) % (h - rows)
+        u, v = d["u"][:, j0:j0 + rows], d["v"][:, j0:j0 + rows]
+        kap = SO.divergence_cumulants(SO.ensemble_moments(u), SO.ensemble_moments(v), 1.0, 1.0)
+        f = SO.surrogate_features(kap, d["isovalues"])
+        SO.mlp_forward(p, f.reshape(-1, 17), SO.surrogate_prior(f).reshape(-1))
+        cells += (rows - 1) * (w - 1)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} bands of {rows} rows x {w} cols x 50 members, K=8 (FP64 numpy, single thread)",
+            "seconds": round(dt, 2)}
+
+
+def learned_arm(args):
+    """Config-5 workload: train the surrogate (untimed), then time moments + fused inference."""
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = False
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = True
+    import paper_2510_01190_gb300 as lib
+    from paper_2510_01190_gb300 import surrogate as G
+    from paper_2510_01190_gb300 import synth
+
+    lib.load()
+    # training (not timed): two other non-Gaussian fields, empirical-mode MC labels at S = 1e4
+    t_train0 = time.perf_counter()
+    parts = []
+    for seed, hh, ww in ((1, 384, 384), (3, 192, 256)):
+        dd = synth.non_gaussian_ensemble(seed, h=hh, w=ww, m=50, k=8)
+        uu, vv = torch.from_numpy(dd["u"]).to(dev), torch.from_numpy(dd["v"]).to(dev)
+        ft, pr = G.lcp_surrogate_features(G.lcp_moments(uu, vv), dd["isovalues"])
+        est, _ = lib.lcp_mc(dd["isovalues"], 10000, 100 + seed, mode="empirical", members=(uu, vv))
+        inner = torch.zeros(est.shape, dtype=torch.bool, device=dev)
+        inner[:, 1:-1, 1:-1] = True
+        sel = inner.reshape(-1)
+        parts.append((ft[sel], pr[sel], est.reshape(-1)[sel]))
+    X, P, T = (torch.cat([q[i] for q in parts]).contiguous() for i in range(3))
+    net = G.Surrogate(synth.mlp_init_params(0, zero_output=True), device=dev)
+    losses = net.fit(X, P, T, epochs=max(1, args.train_epochs), batch=8192, lr=3e-3, lr_final=1e-4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train0
+    del X, P, T, parts
+
+    d = synth.non_gaussian_ensemble(0, h=1024, w=1024, m=50, k=8)
+    iso = d["isovalues"]
+    Mm, Hh, Ww = d["u"].shape
+    Kk, Hc, Wc = len(iso), Hh - 1, Ww - 1
+    u, v = torch.from_numpy(d["u"]).to(dev), torch.from_numpy(d["v"]).to(dev)
+    mom = torch.empty((2, Hh, Ww, 4), dtype=torch.float32, device=dev)
+    out = torch.empty((Kk, Hc, Wc), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        G.lcp_moments(u, v, out=mom)
+        if evs:
+            evs[1].record(stream)
+        net.infer(mom, iso, out=out)
+        if evs:
+            evs[2].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local).start()
+    time.sleep(0.35)
+    n = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n)]
+    if pg:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    for i in range(n):
+        step(ev[i])
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if pg:
+        torch.distributed.barrier()
+    time.sleep(0.25)
+    clocks.stop()
+    total_ms = max_over_ranks(ev[0][0].elapsed_time(ev[-1][2]), device=dev)
+    ms_per_step = total_ms / n
+    mom_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / n
+    inf_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / n
+    value = weak_scaling_value(Hc * Wc, world, ms_per_step)
+    # rooflines: the moments stream (HBM) and the network (bf16 tensor; 2 x (32x64 + 64x64) MACs per row)
+    mom_bytes = 2 * Mm * Hh * Ww * 4 + 2 * Hh * Ww * 16
+    hbm_peak, hbm_kind = measured_hbm_peak()
+    rows = Kk * Hc * Wc
+    flops = rows * 2 * (32 * 64 + 64 * 64 + 64)
+    tc_peak, tc_kind = measured_bf16_peak()
+    roof_mom = {"bound": "hbm", "achieved": round(mom_bytes / (mom_ms / 1e3) / 1e9, 1), "peak": hbm_peak,
+                "unit": "GB/s", "peak_kind": hbm_kind, "kernel": "moments_kernel<float,4>", "kernel_ms": round(mom_ms, 4),
+                "alg_bytes_per_launch": mom_bytes}
+    roof_mom["frac"] = round(roof_mom["achieved"] / hbm_peak, 4)
+    roof_inf = {"bound": "tensor", "achieved": round(flops / (inf_ms / 1e3) / 1e12, 2), "peak": tc_peak,
+                "unit": "TFLOP/s", "peak_kind": tc_kind, "kernel": "mlp_infer_kernel<float> (mma.sync bf16)",
+                "kernel_ms": round(inf_ms, 4), "alg_flops_per_launch": flops}
+    roof_inf["frac"] = round(roof_inf["achieved"] / tc_peak, 4)
+    dominant = roof_mom if mom_ms >= inf_ms else roof_inf
+    traffic = profiled_traffic("lcp_learned_1024_m50_k8.md", ("surrogate.cu", "lcp_common.cuh"))
+    if dominant is roof_mom:
+        traffic = None  # the committed capture's per-step figure is the inference kernel's
+    roof = dict(dominant, traffic=traffic, other=roof_inf if dominant is roof_mom else roof_mom)
+
+    # accuracy against the exact empirical LCP on a crop; equal-error Monte Carlo
+    acc = None
+    if rank == 0 and not args.no_mc:
+        import oracle as O
+
+        y0, x0, cn = 400, 600, 40
+        exact = O.exact_empirical_lcp(d["u"][:, y0:y0 + cn, x0:x0 + cn], d["v"][:, y0:y0 + cn, x0:x0 + cn], 1.0, 1.0,
+                                      iso)
+
+        def err(m):
+            e = m[:, y0 + 1:y0 + cn - 2, x0 + 1:x0 + cn - 2].double().cpu().numpy() - exact
+            return float(np.sqrt((e * e).mean())), float(np.abs(e).max())
+
+        closed, _ = lib.lcp_fused(u, v, iso, 1.0, 1.0, 0)
+        rms_c, max_c = err(closed)
+        rms_l, max_l = err(out)
+        mc = []
+        for S in (100, 1000, 10000):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            est, _ = lib.lcp_mc(iso, S, 7, mode="empirical", members=(u, v))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            r, mx = err(est)
+            mc.append((S, e0.elapsed_time(e1), r, mx))
+        c_rms = float(np.median([r * np.sqrt(S) for S, _, r, _ in mc]))
+        c_max = float(np.median([mx * np.sqrt(S) for S, _, _, mx in mc]))
+        rate = float(np.median([t / S for S, t, _, _ in mc]))  # ms per sample
+        s_rms, s_max = (c_rms / rms_l) ** 2, (c_max / max_l) ** 2
+        acc = {"judge": f"exact empirical LCP, interior cells of a {cn}x{cn} crop",
+               "closed_form_ddof0": {"rms": round(rms_c, 5), "max": round(max_c, 5)},
+               "learned": {"rms": round(rms_l, 5), "max": round(max_l, 5)},
+               "mc": [{"S": S, "ms": round(t, 3), "rms": round(r, 5), "max": round(mx, 5)} for S, t, r, mx in mc],
+               "mc_S_at_learned_rms": round(s_rms), "mc_S_at_learned_max": round(s_max),
+               "t_mc_over_t_learned_at_equal_rms": round(s_rms * rate / ms_per_step, 1),
+               "t_mc_over_t_learned_at_equal_max": round(s_max * rate / ms_per_step, 1),
+               "train_s": round(t_train, 2), "train_final_loss": round(losses[-1], 6)}
+    cpu = learned_cpu_baseline(d) if (not args.no_cpu and rank == 0 and world == 1) else None
+
+    e2e = None
+    if args.e2e_steps > 0:
+        uh, vh = torch.from_numpy(d["u"]).pin_memory(), torch.from_numpy(d["v"]).pin_memory()
+        oh = torch.empty((Kk, Hc, Wc), dtype=torch.float32).pin_memory()
+
+        def host_step():
+            u.copy_(uh, non_blocking=True)
+            v.copy_(vh, non_blocking=True)
+            step()
+            oh.copy_(out, non_blocking=True)
+
+        for _ in range(3):
+            host_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            host_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1) / args.e2e_steps
+        e2e = {"value": world * Hc * Wc / (e_ms / 1e3), "unit": UNIT, "ms_per_step": round(e_ms, 4),
+               "h2d_bytes_per_step": 2 * Mm * Hh * Ww * 4, "d2h_bytes_per_step": Kk * Hc * Wc * 4}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 moments, bf16 network", "data": "synthetic",
+            "config": {"workload": LEARNED_WORKLOAD, "H": Hh, "W": Ww, "M": Mm, "K": Kk, "global_batch": world,
+                       "parallelism": f"independent fields x{world}" if world > 1 else "single",
+                       "l2": "no flush: inputs 419 MB > 129 MB L2", "lcp_values_per_s": value * Kk},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "accuracy": acc,
+            "clocks": clocks.summary(t_wall0, t_wall1), "gpu_launches": 2 * n,
+            "gpu": torch.cuda.get_device_name(dev),
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
     if args.workload == "batch":
         return batch_arm(args)
+    if args.workload == "learned":
+        return learned_arm(args)
     return our_arm(args)
 
 

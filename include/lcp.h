@@ -273,6 +273,94 @@ lcp_status lcp_batch_autotune(const lcp_batch_plan* plan, int reps, lcp_tune* be
                               lcp_stream_t stream);
 
 /*
+ * Learned surrogate for ensembles that are not Gaussian.  The paper mentions
+ * neural surrogates only among related work (Sec. 2); the network, its
+ * features and its training are this library's addition.  Under the empirical
+ * model (every vertex component an independent uniform draw from its own
+ * members), the divergence D of a vertex is the Eq. 1 stencil sum of four
+ * independent values, so its cumulants are sums of the terms' cumulants scaled
+ * by the stencil weights (1/(2dx), or 1/dx at the grid's edges).  A
+ * 17 -> 64 -> 64 -> 1 network (tanh, tanh, sigmoid; BF16 operands, FP32
+ * accumulation on the tensor cores) maps per-cell features of those cumulants
+ * to the LCP.  Features of cell (i, j) and isovalue c, vertices (i, j),
+ * (i+1, j), (i, j+1), (i+1, j+1), sigma = sqrt(k2):
+ *   4v+0 (c - k1)/sigma clipped to [-8, 8] (sigma = 0: -8, 0 or 8 by sign)
+ *   4v+1 sigma / mean of the cell's four sigmas (1 if all are 0)
+ *   4v+2 k3/sigma^3 clipped to [-5, 5];  4v+3 k4/sigma^4 clipped to [-2, 10]
+ *        (both 0 when sigma = 0)
+ *   16   the independent-Gaussian closed-form LCP with means k1, variances k2
+ * A feature row is 32 bf16 values (features 17..31 are zero).  Each row also
+ * has a prior, the logit of feature 16 clamped to [1e-6, 1 - 1e-6], in fp32:
+ * the network's output is y = sigmoid(h2 . w3 + b3 + prior), so that it learns
+ * the correction to the Gaussian closed form in logit space.
+ *
+ * Parameters: one fp32 buffer of LCP_MLP_NPARAMS floats:
+ *   W1 [64][32] at 0     (hidden unit n, feature k; columns 17..31 stay zero)
+ *   b1 [64]     at 2048
+ *   W2 [64][64] at 2112  (output unit n, input unit k)
+ *   b2 [64]     at 6208
+ *   w3 [64]     at 6272
+ *   b3          at 6336  (3 floats of padding follow)
+ */
+#define LCP_MLP_FEAT_STRIDE 32
+#define LCP_MLP_NPARAMS 6340
+
+/*
+ * lcp_moments - plug-in central moments of every vertex component over the
+ * members: mom[comp][j][i] = (mean, m2, m3, m4) as float4 (divisor M), comp 0 =
+ * u, 1 = v; shifted power sums about member 0 in FP32.  mom: device
+ * [2][H][W][4] fp32 (16-byte aligned).  Member arguments as lcp_stats.
+ */
+lcp_status lcp_moments(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
+                       int64_t member_stride, float* mom, lcp_stream_t stream);
+
+/*
+ * lcp_surrogate_features - the network's input rows for every cell and
+ * isovalue: feat[(k (H-1) + j)(W-1) + i][32] bf16 (device, 16-byte aligned)
+ * and their priors prior[same row] fp32 (device, or NULL), from mom
+ * (lcp_moments' layout).  iso: HOST array of K <= 64 fp32 values.
+ */
+lcp_status lcp_surrogate_features(const float* mom, int H, int W, double dx, double dy, const float* iso,
+                                  int K, void* feat, float* prior, lcp_stream_t stream);
+
+/*
+ * lcp_mlp_forward - y[r] = network(feat[r], prior[r]) for r < n (feat bf16
+ * [n][32], prior fp32 [n] or NULL for 0, y fp32 [n], params fp32 as above; all
+ * device).
+ */
+lcp_status lcp_mlp_forward(const float* params, const void* feat, const float* prior, int64_t n, float* y,
+                           lcp_stream_t stream);
+
+/*
+ * lcp_mlp_backward - gradient of the mean squared error
+ * (1/n) sum_r (network(feat[r], prior[r]) - target[r])^2 with respect to every
+ * parameter, written to grad (fp32 [LCP_MLP_NPARAMS], device; overwritten,
+ * padding and the zero columns of W1 get 0).  loss (device fp32 scalar, or
+ * NULL) receives the loss itself.  Weight gradients are contractions over the
+ * rows on the tensor cores, FP32-accumulated.
+ */
+lcp_status lcp_mlp_backward(const float* params, const void* feat, const float* prior, const float* target,
+                            int64_t n, float* grad, float* loss, lcp_stream_t stream);
+
+/*
+ * lcp_adam_step - one Adam update (Kingma and Ba, ICLR 2015, Algorithm 1) of n
+ * fp32 parameters in place: m, v (device, n floats each, zero before step 1)
+ * are the moving averages of grad and grad^2, bias-corrected with step count
+ * t >= 1.
+ */
+lcp_status lcp_adam_step(float* params, const float* grad, float* m, float* v, int64_t n, int t, float lr,
+                         float beta1, float beta2, float eps, lcp_stream_t stream);
+
+/*
+ * lcp_mlp_infer - the learned LCP map from moments: per cell and isovalue the
+ * features above and the network, fused in one kernel (no feature rows in
+ * HBM).  lcp_out [K][H-1][W-1] of out_dtype (LCP_F32 or LCP_F16); iso HOST,
+ * K <= 64.
+ */
+lcp_status lcp_mlp_infer(const float* mom, int H, int W, double dx, double dy, const float* iso, int K,
+                         const float* params, void* lcp_out, lcp_dtype out_dtype, lcp_stream_t stream);
+
+/*
  * lcp_mc - classical Monte Carlo estimate of the LCP map (Sec. 3.2 and Sec. 4):
  * every sample is one realisation of the whole field; its divergence (Eq. 1,
  * same boundary rule) is tested per cell and isovalue, "crossing" meaning

@@ -36,7 +36,11 @@ R14 Features of cell (i, j), isovalue c, vertices in the order (i, j),
     through feature 16; the raw c is not an input, because shifting the field
     and c together leaves the crossing probability unchanged.
 R15 Network: h1 = tanh(x W1 + b1), h2 = tanh(h1 W2 + b2),
-    y = sigmoid(h2 . w3 + b3); loss = mean over rows of (y - t)^2.
+    y = sigmoid(h2 . w3 + b3 + prior), with prior = logit of feature 16 (the
+    Gaussian closed form) clamped to [1e-6, 1 - 1e-6]: the network learns the
+    non-Gaussian correction in logit space, and an untrained output layer
+    (w3 = 0, b3 = 0) reproduces the closed form.  loss = mean over rows of
+    (y - t)^2.
 """
 
 from __future__ import annotations
@@ -50,6 +54,7 @@ __all__ = [
     "ensemble_moments",
     "divergence_cumulants",
     "surrogate_features",
+    "surrogate_prior",
     "mlp_forward",
     "mlp_backward",
     "mse_loss",
@@ -154,6 +159,13 @@ def surrogate_features(kappa, isovalues):
     return out
 
 
+def surrogate_prior(features):
+    """The network's prior of every row (reading R15): logit of feature 16,
+    clamped to [1e-6, 1 - 1e-6].  features [..., 17];  returns [...]"""
+    g = np.clip(np.asarray(features, np.float64)[..., 16], 1e-6, 1.0 - 1e-6)
+    return np.log(g) - np.log1p(-g)
+
+
 # --------------------------------------------------------------------------
 # The network (reading R15) and its training arithmetic
 # --------------------------------------------------------------------------
@@ -161,17 +173,19 @@ def _sigmoid(z):
     return 1.0 / (1.0 + np.exp(-z))
 
 
-def mlp_forward(params, x):
-    """y = sigmoid(tanh(tanh(x W1 + b1) W2 + b2) . w3 + b3).
+def mlp_forward(params, x, prior=None):
+    """y = sigmoid(tanh(tanh(x W1 + b1) W2 + b2) . w3 + b3 + prior).
 
     params : dict W1 [17, 64], b1 [64], W2 [64, 64], b2 [64], w3 [64], b3 scalar
-    x      : [N, 17]
+    x      : [N, 17];  prior : [N] or None (zero)
     returns (y [N], cache)
     """
     x = np.asarray(x, np.float64)
     h1 = np.tanh(x @ params["W1"] + params["b1"])
     h2 = np.tanh(h1 @ params["W2"] + params["b2"])
     z3 = h2 @ params["w3"] + params["b3"]
+    if prior is not None:
+        z3 = z3 + np.asarray(prior, np.float64)
     y = _sigmoid(z3)
     return y, dict(x=x, h1=h1, h2=h2, y=y)
 

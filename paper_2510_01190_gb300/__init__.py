@@ -13,3 +13,4 @@ CPU fallback.
 
 from ._binding import *  # noqa: F401,F403
 from ._binding import __all__  # noqa: F401
+from . import surrogate  # noqa: E402,F401  (learned surrogate: moments, features, network kernels)

@@ -1,0 +1,804 @@
+// Learned surrogate: moments of the members, cumulants of the vertex
+// divergence under the empirical model, per-cell features, and a
+// 17 -> 64 -> 64 -> 1 network trained and evaluated on the tensor cores
+// (mma.sync m16n8k16, BF16 operands, FP32 accumulation).
+//
+// Register layouts of mma.sync.m16n8k16 (gid = lane / 4, tig = lane % 4):
+//   A (16 x 16, row-major):  a0 = A[gid][2 tig .. +1],     a1 = A[gid+8][2 tig ..],
+//                            a2 = A[gid][8 + 2 tig ..],    a3 = A[gid+8][8 + 2 tig ..]
+//   B (16 x 8, k x n):       b0 = B[2 tig .. +1][gid],     b1 = B[8 + 2 tig .. +1][gid]
+//   C (16 x 8, fp32):        c0, c1 = C[gid][2 tig .. +1], c2, c3 = C[gid+8][2 tig .. +1]
+// so the C fragments of two adjacent 8-column tiles are exactly the A fragment
+// of the next layer's 16-wide k-step (no shared-memory round trip between
+// layers).
+#include <cmath>
+#include <cstddef>
+#include <mutex>
+
+#include "lcp_common.cuh"
+
+namespace lcp {
+namespace {
+
+constexpr int kHid = 64;
+constexpr int kFS = LCP_MLP_FEAT_STRIDE;  // 32 bf16 per feature row
+constexpr int kOffW1 = 0, kOffB1 = 2048, kOffW2 = 2112, kOffB2 = 6208, kOffW3 = 6272, kOffB3 = 6336;
+constexpr int kW1S = 40;  // shared-memory row strides (bf16) chosen so that fragment loads hit 32 banks
+constexpr int kW2S = 72;
+
+// ---- 1. moments ---------------------------------------------------------------
+// Shifted power sums about member 0, then the central moments by the binomial
+// expansion: with delta = S1/M and e_p = S_p/M,
+//   m2 = e2 - delta^2,  m3 = e3 - 3 delta e2 + 2 delta^3,
+//   m4 = e4 - 4 delta e3 + 6 delta^2 e2 - 3 delta^4.
+template <typename T, int VEC>
+__global__ void __launch_bounds__(256) moments_kernel(const T* __restrict__ u, const T* __restrict__ v, int M,
+                                                     int64_t stride, int64_t n_vert, int vec_ok, float4* mom) {
+    using L = Loader<T, VEC>;
+    const float fm = (float)M;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g * VEC < n_vert;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n0 = g * VEC;
+        const int cnt = (int)min((int64_t)VEC, n_vert - n0);
+        const bool vec = vec_ok && cnt == VEC;
+        for (int comp = 0; comp < 2; ++comp) {
+            const T* x = comp ? v : u;
+            float x0[VEC], s[4][VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                x0[e] = 0.f;
+                s[0][e] = s[1][e] = s[2][e] = s[3][e] = 0.f;
+            }
+            if (vec) {
+                L::cvt(L::load(x + n0), x0);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e)
+                    if (e < cnt) Loader<T, 1>::cvt(Loader<T, 1>::load(x + n0 + e), &x0[e]);
+            }
+            for (int m = 1; m < M; ++m) {
+                float a[VEC];
+                if (vec) {
+                    L::cvt(L::load(x + (int64_t)m * stride + n0), a);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        a[e] = 0.f;
+                        if (e < cnt) Loader<T, 1>::cvt(Loader<T, 1>::load(x + (int64_t)m * stride + n0 + e), &a[e]);
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const float d = a[e] - x0[e], d2 = d * d;
+                    s[0][e] += d;
+                    s[1][e] += d2;
+                    s[2][e] = fmaf(d2, d, s[2][e]);
+                    s[3][e] = fmaf(d2, d2, s[3][e]);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                if (e >= cnt) break;
+                const float dl = s[0][e] / fm, e2 = s[1][e] / fm, e3 = s[2][e] / fm, e4 = s[3][e] / fm;
+                const float dl2 = dl * dl;
+                float m2 = e2 - dl2;
+                float m3 = e3 - 3.f * dl * e2 + 2.f * dl2 * dl;
+                float m4 = e4 - 4.f * dl * e3 + 6.f * dl2 * e2 - 3.f * dl2 * dl2;
+                m2 = m2 < 0.f ? 0.f : m2;  // NaN stays NaN
+                m4 = m4 < 0.f ? 0.f : m4;
+                mom[(int64_t)comp * n_vert + n0 + e] = make_float4(x0[e] + dl, m2, m3, m4);
+            }
+        }
+    }
+}
+
+// ---- 2. cumulants of the vertex divergence ------------------------------------
+// k_n(D) = a^n k_n(U_hi) + (-a)^n k_n(U_lo) + b^n k_n(V_hi) + (-b)^n k_n(V_lo),
+// a = 1/(2 dx) inside and 1/dx on the first/last column (b likewise along y),
+// with k1 = mean, k2 = m2, k3 = m3, k4 = m4 - 3 m2^2 of each term.
+__device__ __forceinline__ float4 vertex_cumulants(const float4* __restrict__ mu, const float4* __restrict__ mv,
+                                                   int H, int W, int j, int i, const Spacing& sp) {
+    const int ilo = max(i - 1, 0), ihi = min(i + 1, W - 1), jlo = max(j - 1, 0), jhi = min(j + 1, H - 1);
+    const float a = (ihi - ilo == 2) ? sp.sx2 : sp.sx1, b = (jhi - jlo == 2) ? sp.sy2 : sp.sy1;
+    const float4 A = __ldg(mu + (int64_t)j * W + ihi), B = __ldg(mu + (int64_t)j * W + ilo);
+    const float4 C = __ldg(mv + (int64_t)jhi * W + i), D = __ldg(mv + (int64_t)jlo * W + i);
+    const float a2 = a * a, b2 = b * b;
+    float4 k;
+    k.x = fmaf(a, A.x - B.x, b * (C.x - D.x));
+    k.y = fmaf(a2, A.y + B.y, b2 * (C.y + D.y));
+    k.z = fmaf(a2 * a, A.z - B.z, b2 * b * (C.z - D.z));
+    const float ka = (A.w - 3.f * A.y * A.y) + (B.w - 3.f * B.y * B.y);
+    const float kb = (C.w - 3.f * C.y * C.y) + (D.w - 3.f * D.y * D.y);
+    k.w = fmaf(a2 * a2, ka, b2 * b2 * kb);
+    return k;
+}
+
+// Isovalue-independent part of a cell's features.
+struct CellPart {
+    float mu[4], sig[4], ratio[4], skew[4], kurt[4], var[4];
+};
+
+__device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
+
+__device__ __forceinline__ CellPart cell_part(const float4 (&k)[4]) {
+    CellPart p;
+    float msum = 0.f;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        p.mu[v] = k[v].x;
+        p.var[v] = fmaxf(k[v].y, 0.f);
+        p.sig[v] = sqrtf(p.var[v]);
+        msum += p.sig[v];
+    }
+    const float mean_sig = 0.25f * msum;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const float s = p.sig[v];
+        p.ratio[v] = mean_sig > 0.f ? s / mean_sig : 1.f;
+        if (s > 0.f) {
+            const float s2 = s * s;
+            p.skew[v] = clampf(k[v].z / (s2 * s), -5.f, 5.f);
+            p.kurt[v] = clampf(k[v].w / (s2 * s2), -2.f, 10.f);
+        } else {
+            p.skew[v] = 0.f;
+            p.kurt[v] = 0.f;
+        }
+    }
+    return p;
+}
+
+// The network's prior: the logit of the independent-Gaussian LCP, clamped to
+// [1e-6, 1 - 1e-6] (|logit| <= 13.8); the output layer adds it to its own sum.
+__device__ __forceinline__ float prior_logit(float g) {
+    const float p = fminf(fmaxf(g, 1e-6f), 1.0f - 1e-6f);
+    return __logf(p) - __logf(1.0f - p);
+}
+
+// The 17 features of (cell, c), bf16, into a 32-wide row (16-byte aligned);
+// returns the prior (fp32).
+__device__ __forceinline__ float cell_features(const CellPart& p, float c, __nv_bfloat16* row) {
+    float f[kFS];
+#pragma unroll
+    for (int q = 0; q < kFS; ++q) f[q] = 0.f;
+    float pb = 1.f, qb = 1.f;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const float d = c - p.mu[v];
+        f[4 * v + 0] = p.sig[v] > 0.f ? clampf(d / p.sig[v], -8.f, 8.f) : (d > 0.f ? 8.f : (d < 0.f ? -8.f : 0.f));
+        f[4 * v + 1] = p.ratio[v];
+        f[4 * v + 2] = p.skew[v];
+        f[4 * v + 3] = p.kurt[v];
+        float pv, qv;
+        below_above(p.mu[v], p.var[v], c, pv, qv);
+        pb *= pv;
+        qb *= qv;
+    }
+    f[16] = 1.f - pb - qb;
+    uint4* out = reinterpret_cast<uint4*>(row);
+#pragma unroll
+    for (int q = 0; q < kFS / 8; ++q) {
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(f[8 * q + 2 * e], f[8 * q + 2 * e + 1]);
+            w[e] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        out[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    return prior_logit(f[16]);
+}
+
+__global__ void __launch_bounds__(256) features_kernel(const float4* __restrict__ mom, int H, int W, Spacing sp,
+                                                      const __grid_constant__ IsoParams iso, __nv_bfloat16* feat,
+                                                      float* prior) {
+    const int Hc = H - 1, Wc = W - 1;
+    const int64_t n_cells = (int64_t)Hc * Wc, n_vert = (int64_t)H * W;
+    for (int64_t cidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cidx < n_cells;
+         cidx += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(cidx / Wc), i = (int)(cidx - (int64_t)j * Wc);
+        float4 k[4];
+        k[0] = vertex_cumulants(mom, mom + n_vert, H, W, j, i, sp);
+        k[1] = vertex_cumulants(mom, mom + n_vert, H, W, j, i + 1, sp);
+        k[2] = vertex_cumulants(mom, mom + n_vert, H, W, j + 1, i, sp);
+        k[3] = vertex_cumulants(mom, mom + n_vert, H, W, j + 1, i + 1, sp);
+        const CellPart p = cell_part(k);
+        for (int q = 0; q < iso.K; ++q) {
+            const int64_t r = (int64_t)q * n_cells + cidx;
+            const float pr = cell_features(p, iso.c[q], feat + r * kFS);
+            if (prior) prior[r] = pr;
+        }
+    }
+}
+
+// ---- 3. tensor-core building blocks -------------------------------------------
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Four 8x8 bf16 matrices; lane l supplies the row address of matrix l / 8.
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ float2 unpack_bf16(uint32_t w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+}
+__device__ __forceinline__ float tanh_fast(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sigmoid(float z) { return 1.0f / (1.0f + __expf(-z)); }
+
+// Network weights in shared memory, BF16 operands and FP32 vectors.
+struct NetSmem {
+    __align__(16) __nv_bfloat16 W1[kHid * kW1S];  // [n][k]
+    __align__(16) __nv_bfloat16 W2[kHid * kW2S];  // [n][k]
+    __align__(16) float b1[kHid];
+    float b2[kHid], w3[kHid];
+    float b3;
+};
+
+__device__ void load_net(const float* __restrict__ prm, NetSmem& s, __nv_bfloat16* W2t /* [k][n], or null */) {
+    for (int q = threadIdx.x; q < kHid * kFS; q += blockDim.x) {
+        const int n = q / kFS, k = q - n * kFS;
+        s.W1[n * kW1S + k] = __float2bfloat16_rn(k < 17 ? prm[kOffW1 + q] : 0.f);
+    }
+    for (int q = threadIdx.x; q < kHid * kHid; q += blockDim.x) {
+        const int n = q >> 6, k = q & 63;
+        const __nv_bfloat16 w = __float2bfloat16_rn(prm[kOffW2 + q]);
+        s.W2[n * kW2S + k] = w;
+        if (W2t) W2t[k * kW2S + n] = w;
+    }
+    for (int q = threadIdx.x; q < kHid; q += blockDim.x) {
+        s.b1[q] = prm[kOffB1 + q];
+        s.b2[q] = prm[kOffB2 + q];
+        s.w3[q] = prm[kOffW3 + q];
+    }
+    if (threadIdx.x == 0) s.b3 = prm[kOffB3];
+}
+
+// One warp, 16 rows: layers 1 and 2 from the A fragments of the input (two
+// 16-feature k-steps).  Leaves h1 as bf16 A fragments (four 16-unit k-steps)
+// and h2 in C-fragment layout (fp32).
+__device__ __forceinline__ void forward16(const NetSmem& s, const uint32_t (&x)[2][4], uint32_t (&h1)[4][4],
+                                          float (&h2)[8][4], int gid, int tig) {
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const float bl = s.b1[8 * nt + 2 * tig], bh = s.b1[8 * nt + 2 * tig + 1];
+        acc[nt][0] = bl; acc[nt][1] = bh; acc[nt][2] = bl; acc[nt][3] = bh;
+    }
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const __nv_bfloat16* w = s.W1 + (8 * nt + gid) * kW1S + 16 * ks + 2 * tig;
+            mma16816(acc[nt], x[ks], *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
+        }
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+        const int a = 2 * ks, b = 2 * ks + 1;
+        h1[ks][0] = pack_bf16(tanh_fast(acc[a][0]), tanh_fast(acc[a][1]));
+        h1[ks][1] = pack_bf16(tanh_fast(acc[a][2]), tanh_fast(acc[a][3]));
+        h1[ks][2] = pack_bf16(tanh_fast(acc[b][0]), tanh_fast(acc[b][1]));
+        h1[ks][3] = pack_bf16(tanh_fast(acc[b][2]), tanh_fast(acc[b][3]));
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const float bl = s.b2[8 * nt + 2 * tig], bh = s.b2[8 * nt + 2 * tig + 1];
+        h2[nt][0] = bl; h2[nt][1] = bh; h2[nt][2] = bl; h2[nt][3] = bh;
+    }
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const __nv_bfloat16* w = s.W2 + (8 * nt + gid) * kW2S + 16 * ks + 2 * tig;
+            mma16816(h2[nt], h1[ks], *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
+        }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) h2[nt][e] = tanh_fast(h2[nt][e]);
+}
+
+// Output pre-activation of rows gid and gid + 8 (complete in all four lanes of the group).
+__device__ __forceinline__ float2 output16(const NetSmem& s, const float (&h2)[8][4], int tig) {
+    float lo = 0.f, hi = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const float w0 = s.w3[8 * nt + 2 * tig], w1 = s.w3[8 * nt + 2 * tig + 1];
+        lo = fmaf(h2[nt][0], w0, fmaf(h2[nt][1], w1, lo));
+        hi = fmaf(h2[nt][2], w0, fmaf(h2[nt][3], w1, hi));
+    }
+    lo += __shfl_xor_sync(0xFFFFFFFFu, lo, 1);
+    hi += __shfl_xor_sync(0xFFFFFFFFu, hi, 1);
+    lo += __shfl_xor_sync(0xFFFFFFFFu, lo, 2);
+    hi += __shfl_xor_sync(0xFFFFFFFFu, hi, 2);
+    return make_float2(lo + s.b3, hi + s.b3);
+}
+
+// A fragments of a 16-row x 32-feature tile held row-major in shared memory
+// (row stride kW1S bf16): matrices (rows 0-7 | 8-15) x (k 0-7 | 8-15) per k-step.
+__device__ __forceinline__ void load_x_frags(const __nv_bfloat16* tile, uint32_t (&x)[2][4], int lane) {
+    const int r = (lane & 7) + ((lane >> 3) & 1) * 8, c = (lane >> 4) * 8;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) ldsm_x4(x[ks], tile + r * kW1S + 16 * ks + c);
+}
+
+// ---- 4. forward over feature rows ---------------------------------------------
+constexpr int kMT = 128;  // threads per CTA of the network kernels (4 warps)
+
+__global__ void __launch_bounds__(kMT) mlp_forward_kernel(const float* __restrict__ prm,
+                                                         const __nv_bfloat16* __restrict__ feat,
+                                                         const float* __restrict__ prior, int64_t n,
+                                                         float* __restrict__ y) {
+    __shared__ NetSmem s;
+    __shared__ __align__(16) __nv_bfloat16 xs[kMT / 32][16 * kW1S];
+    load_net(prm, s, nullptr);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
+    __nv_bfloat16* tile = xs[warp];
+    for (int64_t r0 = ((int64_t)blockIdx.x * (kMT / 32) + warp) * 16; r0 < n;
+         r0 += (int64_t)gridDim.x * (kMT / 32) * 16) {
+        // stage 16 rows (64 B each): lane covers half a row
+        {
+            const int r = lane >> 1, h = lane & 1;
+            uint4 a = make_uint4(0, 0, 0, 0), b = a;
+            if (r0 + r < n) {
+                const uint4* src = reinterpret_cast<const uint4*>(feat + (r0 + r) * kFS) + 2 * h;
+                a = __ldg(src);
+                b = __ldg(src + 1);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(tile + r * kW1S + 16 * h);
+            dst[0] = a;
+            dst[1] = b;
+        }
+        __syncwarp();
+        uint32_t x[2][4], h1[4][4];
+        float h2[8][4];
+        load_x_frags(tile, x, lane);
+        forward16(s, x, h1, h2, gid, tig);
+        const float2 z = output16(s, h2, tig);
+        if (tig == 0) {
+            if (r0 + gid < n) y[r0 + gid] = sigmoid(z.x + (prior ? __ldg(prior + r0 + gid) : 0.f));
+            if (r0 + gid + 8 < n) y[r0 + gid + 8] = sigmoid(z.y + (prior ? __ldg(prior + r0 + gid + 8) : 0.f));
+        }
+        __syncwarp();
+    }
+}
+
+// ---- 5. fused inference from moments ------------------------------------------
+// CTA: 4 cell rows x 32 cell columns, one warp per cell row, one lane per cell.
+// The cumulants of the tile's 5 x 33 vertices are computed once into shared
+// memory; per isovalue each lane writes its cell's feature row, and the warp
+// evaluates its 32 rows as two 16-row tensor-core tiles.
+constexpr int kIR = 4, kIC = 32;
+
+template <typename OutT>
+__global__ void __launch_bounds__(kMT) mlp_infer_kernel(const float4* __restrict__ mom, int H, int W, Spacing sp,
+                                                       const __grid_constant__ IsoParams iso,
+                                                       const float* __restrict__ prm, OutT* __restrict__ out) {
+    __shared__ NetSmem s;
+    __shared__ float4 kap[(kIR + 1) * (kIC + 1)];
+    __shared__ __align__(16) __nv_bfloat16 xs[kMT / 32][32 * kW1S];
+    load_net(prm, s, nullptr);
+    const int Hc = H - 1, Wc = W - 1;
+    const int a = blockIdx.y * kIR, c0 = blockIdx.x * kIC;
+    const int64_t n_vert = (int64_t)H * W;
+    for (int q = threadIdx.x; q < (kIR + 1) * (kIC + 1); q += blockDim.x) {
+        const int rr = q / (kIC + 1), cc = q - rr * (kIC + 1);
+        const int j = min(a + rr, H - 1), i = min(c0 + cc, W - 1);
+        kap[q] = vertex_cumulants(mom, mom + n_vert, H, W, j, i, sp);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
+    const int j = a + warp, i = c0 + lane;
+    const bool ok = j < Hc && i < Wc;
+    float4 k4[4];
+    k4[0] = kap[warp * (kIC + 1) + lane];
+    k4[1] = kap[warp * (kIC + 1) + lane + 1];
+    k4[2] = kap[(warp + 1) * (kIC + 1) + lane];
+    k4[3] = kap[(warp + 1) * (kIC + 1) + lane + 1];
+    const CellPart part = cell_part(k4);
+    __nv_bfloat16* tile = xs[warp];
+    const int64_t plane = (int64_t)Hc * Wc;
+    for (int q = 0; q < iso.K; ++q) {
+        const float pr = cell_features(part, iso.c[q], tile + lane * kW1S);
+        __syncwarp();
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            uint32_t x[2][4], h1[4][4];
+            float h2[8][4];
+            load_x_frags(tile + 16 * mt * kW1S, x, lane);
+            forward16(s, x, h1, h2, gid, tig);
+            const float2 z = output16(s, h2, tig);
+            const float plo = __shfl_sync(0xFFFFFFFFu, pr, 16 * mt + gid);
+            const float phi = __shfl_sync(0xFFFFFFFFu, pr, 16 * mt + gid + 8);
+            if (tig == 0 && j < Hc) {
+                const int i0 = c0 + 16 * mt + gid;
+                OutT* o = out + (int64_t)q * plane + (int64_t)j * Wc;
+                if (i0 < Wc) o[i0] = to_out<OutT>(sigmoid(z.x + plo));
+                if (i0 + 8 < Wc) o[i0 + 8] = to_out<OutT>(sigmoid(z.y + phi));
+            }
+        }
+        __syncwarp();
+    }
+    (void)ok;
+}
+
+// ---- 6. backward: gradient of the mean squared error ---------------------------
+// Per iteration a CTA takes 64 rows (16 per warp).  Each warp runs the forward
+// pass, the output and hidden-layer deltas (dA1 = dZ2 W2^T on the tensor cores,
+// dZ2 in registers as its A fragments), and stages X, h1, dZ1, dZ2 (bf16) in
+// shared memory; the CTA then accumulates the weight gradients
+// dW2 = dZ2^T h1 and dW1 = dZ1^T X as contractions over the 64 rows
+// (ldmatrix .trans supplies the transposed operands), in registers across
+// iterations, and adds them to the output once at the end.
+struct BwdSmem {
+    NetSmem net;
+    __align__(16) __nv_bfloat16 W2t[kHid * kW2S];  // [k][n] = W2[n][k]
+    __align__(16) __nv_bfloat16 xs[64 * kW1S];
+    __align__(16) __nv_bfloat16 h1s[64 * kW2S];
+    __align__(16) __nv_bfloat16 d1s[64 * kW2S];
+    __align__(16) __nv_bfloat16 d2s[64 * kW2S];
+    __align__(16) float db1[kHid];
+    float db2[kHid], dw3[kHid];
+    float db3, loss;
+};
+
+static_assert(offsetof(BwdSmem, xs) % 16 == 0 && offsetof(BwdSmem, h1s) % 16 == 0 &&
+                  offsetof(BwdSmem, d1s) % 16 == 0 && offsetof(BwdSmem, d2s) % 16 == 0,
+              "ldmatrix rows must be 16-byte aligned");
+static_assert((kW1S * 2) % 16 == 0 && (kW2S * 2) % 16 == 0, "row strides must keep 16-byte alignment");
+
+__device__ __forceinline__ void st_pair(__nv_bfloat16* base, int row, int col, int stride, uint32_t w) {
+    *reinterpret_cast<uint32_t*>(base + row * stride + col) = w;
+}
+
+// Column sums over the 8 row groups of a warp (lanes with equal tig).
+__device__ __forceinline__ float sum_over_gid(float x) {
+    x += __shfl_xor_sync(0xFFFFFFFFu, x, 4);
+    x += __shfl_xor_sync(0xFFFFFFFFu, x, 8);
+    x += __shfl_xor_sync(0xFFFFFFFFu, x, 16);
+    return x;
+}
+
+__global__ void __launch_bounds__(kMT) mlp_backward_kernel(const float* __restrict__ prm,
+                                                          const __nv_bfloat16* __restrict__ feat,
+                                                          const float* __restrict__ prior,
+                                                          const float* __restrict__ target, int64_t n,
+                                                          float* __restrict__ grad, float* __restrict__ loss) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
+    load_net(prm, S.net, S.W2t);
+    for (int q = threadIdx.x; q < kHid; q += blockDim.x) S.db1[q] = S.db2[q] = S.dw3[q] = 0.f;
+    if (threadIdx.x == 0) S.db3 = S.loss = 0.f;
+    __syncthreads();
+    const NetSmem& s = S.net;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
+    const float inv_n = 1.0f / (float)n;
+    float gW2[8][4], gW1[4][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) gW2[a][0] = gW2[a][1] = gW2[a][2] = gW2[a][3] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) gW1[a][0] = gW1[a][1] = gW1[a][2] = gW1[a][3] = 0.f;
+    const int rw = 16 * warp;  // this warp's rows inside the staged 64
+
+    for (int64_t base = (int64_t)blockIdx.x * 64; base < n; base += (int64_t)gridDim.x * 64) {
+        const int64_t r0 = base + rw;
+        {  // stage X
+            const int r = lane >> 1, h = lane & 1;
+            uint4 a = make_uint4(0, 0, 0, 0), b = a;
+            if (r0 + r < n) {
+                const uint4* src = reinterpret_cast<const uint4*>(feat + (r0 + r) * kFS) + 2 * h;
+                a = __ldg(src);
+                b = __ldg(src + 1);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(S.xs + (rw + r) * kW1S + 16 * h);
+            dst[0] = a;
+            dst[1] = b;
+        }
+        __syncwarp();
+        uint32_t x[2][4], h1[4][4];
+        float h2[8][4];
+        load_x_frags(S.xs + rw * kW1S, x, lane);
+        forward16(s, x, h1, h2, gid, tig);
+        const float2 z = output16(s, h2, tig);
+        const bool vlo = r0 + gid < n, vhi = r0 + gid + 8 < n;
+        const float plo = (prior && vlo) ? __ldg(prior + r0 + gid) : 0.f;
+        const float phi = (prior && vhi) ? __ldg(prior + r0 + gid + 8) : 0.f;
+        const float ylo = sigmoid(z.x + plo), yhi = sigmoid(z.y + phi);
+        const float tlo = vlo ? __ldg(target + r0 + gid) : 0.f, thi = vhi ? __ldg(target + r0 + gid + 8) : 0.f;
+        // d(sum of squared errors)/dz3 = 2 (y - t) y (1 - y); the 1/n of the mean is applied once at the end
+        const float dlo = vlo ? 2.f * (ylo - tlo) * ylo * (1.f - ylo) : 0.f;
+        const float dhi = vhi ? 2.f * (yhi - thi) * yhi * (1.f - yhi) : 0.f;
+        if (tig == 0) {
+            const float e = (vlo ? (ylo - tlo) * (ylo - tlo) : 0.f) + (vhi ? (yhi - thi) * (yhi - thi) : 0.f);
+            atomicAdd(&S.loss, e);
+            atomicAdd(&S.db3, dlo + dhi);
+        }
+        // stage h1 (its A fragments are C fragments of 8-column tiles 2ks, 2ks+1)
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+            st_pair(S.h1s, rw + gid, 16 * ks + 2 * tig, kW2S, h1[ks][0]);
+            st_pair(S.h1s, rw + gid + 8, 16 * ks + 2 * tig, kW2S, h1[ks][1]);
+            st_pair(S.h1s, rw + gid, 16 * ks + 8 + 2 * tig, kW2S, h1[ks][2]);
+            st_pair(S.h1s, rw + gid + 8, 16 * ks + 8 + 2 * tig, kW2S, h1[ks][3]);
+        }
+        // dZ2 = dz3 w3 (1 - h2^2); dw3 += h2^T dz3; db2 += column sums of dZ2
+        uint32_t d2[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float dz[4];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int col = 8 * nt + 2 * tig + e;
+                const float w = s.w3[col];
+                dz[e] = dlo * w * (1.f - h2[nt][e] * h2[nt][e]);
+                dz[2 + e] = dhi * w * (1.f - h2[nt][2 + e] * h2[nt][2 + e]);
+                const float gw3 = sum_over_gid(h2[nt][e] * dlo + h2[nt][2 + e] * dhi);
+                const float gb2 = sum_over_gid(dz[e] + dz[2 + e]);
+                if (gid == 0) {
+                    atomicAdd(&S.dw3[col], gw3);
+                    atomicAdd(&S.db2[col], gb2);
+                }
+            }
+            const uint32_t lo = pack_bf16(dz[0], dz[1]), hi = pack_bf16(dz[2], dz[3]);
+            d2[nt >> 1][(nt & 1) * 2 + 0] = lo;
+            d2[nt >> 1][(nt & 1) * 2 + 1] = hi;
+            st_pair(S.d2s, rw + gid, 8 * nt + 2 * tig, kW2S, lo);
+            st_pair(S.d2s, rw + gid + 8, 8 * nt + 2 * tig, kW2S, hi);
+        }
+        // dA1 = dZ2 W2^T; B(k = output unit, n = input unit) = W2t[n][k]
+        float da[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) da[nt][0] = da[nt][1] = da[nt][2] = da[nt][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const __nv_bfloat16* w = S.W2t + (8 * nt + gid) * kW2S + 16 * ks + 2 * tig;
+                mma16816(da[nt], d2[ks], *reinterpret_cast<const uint32_t*>(w),
+                         *reinterpret_cast<const uint32_t*>(w + 8));
+            }
+        // dZ1 = dA1 (1 - h1^2); db1 += column sums
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const float2 hl = unpack_bf16(h1[nt >> 1][(nt & 1) * 2 + 0]);
+            const float2 hh = unpack_bf16(h1[nt >> 1][(nt & 1) * 2 + 1]);
+            const float z0 = da[nt][0] * (1.f - hl.x * hl.x), z1 = da[nt][1] * (1.f - hl.y * hl.y);
+            const float z2 = da[nt][2] * (1.f - hh.x * hh.x), z3 = da[nt][3] * (1.f - hh.y * hh.y);
+            st_pair(S.d1s, rw + gid, 8 * nt + 2 * tig, kW2S, pack_bf16(z0, z1));
+            st_pair(S.d1s, rw + gid + 8, 8 * nt + 2 * tig, kW2S, pack_bf16(z2, z3));
+            const float g0 = sum_over_gid(z0 + z2), g1 = sum_over_gid(z1 + z3);
+            if (gid == 0) {
+                atomicAdd(&S.db1[8 * nt + 2 * tig], g0);
+                atomicAdd(&S.db1[8 * nt + 2 * tig + 1], g1);
+            }
+        }
+        __syncthreads();
+        // weight gradients over the 64 staged rows: this warp's 16 output rows
+        const int o0 = 16 * warp;
+        const int ar = (lane & 7) + ((lane >> 4) & 1) * 8, ac = ((lane >> 3) & 1) * 8;  // A^T operand addressing
+        const int br = (lane & 7) + ((lane >> 3) & 1) * 8, bc = (lane >> 4) * 8;        // B operand addressing
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            uint32_t a2[4], a1[4];
+            ldsm_x4_t(a2, S.d2s + (16 * kk + ar) * kW2S + o0 + ac);
+            ldsm_x4_t(a1, S.d1s + (16 * kk + ar) * kW2S + o0 + ac);
+#pragma unroll
+            for (int np = 0; np < 4; ++np) {  // dW2: input units in pairs of 8-column tiles
+                uint32_t b[4];
+                ldsm_x4_t(b, S.h1s + (16 * kk + br) * kW2S + 16 * np + bc);
+                mma16816(gW2[2 * np], a2, b[0], b[1]);
+                mma16816(gW2[2 * np + 1], a2, b[2], b[3]);
+            }
+#pragma unroll
+            for (int np = 0; np < 2; ++np) {  // dW1: features 0-15, 16-31
+                uint32_t b[4];
+                ldsm_x4_t(b, S.xs + (16 * kk + br) * kW1S + 16 * np + bc);
+                mma16816(gW1[2 * np], a1, b[0], b[1]);
+                mma16816(gW1[2 * np + 1], a1, b[2], b[3]);
+            }
+        }
+        __syncthreads();
+    }
+    // add this CTA's sums to the output
+    const int o0 = 16 * warp;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int col = 8 * nt + 2 * tig + e;
+            atomicAdd(grad + kOffW2 + (o0 + gid) * kHid + col, gW2[nt][e] * inv_n);
+            atomicAdd(grad + kOffW2 + (o0 + gid + 8) * kHid + col, gW2[nt][2 + e] * inv_n);
+        }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int col = 8 * nt + 2 * tig + e;
+            if (col < 17) {
+                atomicAdd(grad + kOffW1 + (o0 + gid) * kFS + col, gW1[nt][e] * inv_n);
+                atomicAdd(grad + kOffW1 + (o0 + gid + 8) * kFS + col, gW1[nt][2 + e] * inv_n);
+            }
+        }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kHid; q += blockDim.x) {
+        atomicAdd(grad + kOffB1 + q, S.db1[q] * inv_n);
+        atomicAdd(grad + kOffB2 + q, S.db2[q] * inv_n);
+        atomicAdd(grad + kOffW3 + q, S.dw3[q] * inv_n);
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(grad + kOffB3, S.db3 * inv_n);
+        if (loss) atomicAdd(loss, S.loss * inv_n);
+    }
+}
+
+// ---- 7. Adam ---------------------------------------------------------------------
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const float gq = g[q];
+        const float mq = b1 * m[q] + (1.f - b1) * gq;
+        const float vq = b2 * v[q] + (1.f - b2) * gq * gq;
+        m[q] = mq;
+        v[q] = vq;
+        p[q] -= lr * (mq * c1) / (sqrtf(vq * c2) + eps);
+    }
+}
+
+}  // namespace
+}  // namespace lcp
+
+// ---- host ------------------------------------------------------------------------
+using namespace lcp;
+
+namespace {
+
+lcp_status check_iso_host(const char* fn, const float* iso, int K, IsoParams& ip) {
+    if (!iso) return fail(LCP_ERR_ARG, "%s: iso must be a non-NULL host array", fn);
+    if (K < 1 || K > kMaxIsoPerLaunch) return fail(LCP_ERR_ARG, "%s: need 1 <= K <= %d", fn, kMaxIsoPerLaunch);
+    ip.K = K;
+    for (int k = 0; k < K; ++k) ip.c[k] = iso[k];
+    return LCP_OK;
+}
+
+int grid_for(int64_t work, int per_block, int cap_per_sm) {
+    const int64_t b = (work + per_block - 1) / per_block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * cap_per_sm));
+}
+
+}  // namespace
+
+extern "C" lcp_status lcp_moments(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
+                                  int64_t member_stride, float* mom, lcp_stream_t stream) {
+    lcp_status s = check_members("lcp_moments", u, v, in_dtype, M, H, W, member_stride, 0);
+    if (s != LCP_OK) return s;
+    if (!mom || !aligned16(mom)) return fail(LCP_ERR_ARG, "lcp_moments: mom must be a 16-byte aligned device array");
+    const int64_t nv = (int64_t)H * W;
+    const int64_t stride = M > 1 ? member_stride : nv;
+    float4* out = reinterpret_cast<float4*>(mom);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool in16 = aligned16(u) && aligned16(v);
+    if (in_dtype == LCP_F32) {
+        moments_kernel<float, 4><<<grid_for((nv + 3) / 4, 256, 8), 256, 0, st>>>(
+            (const float*)u, (const float*)v, M, stride, nv, in16 && stride % 4 == 0, out);
+    } else {
+        moments_kernel<__nv_bfloat16, 8><<<grid_for((nv + 7) / 8, 256, 8), 256, 0, st>>>(
+            (const __nv_bfloat16*)u, (const __nv_bfloat16*)v, M, stride, nv, in16 && stride % 8 == 0, out);
+    }
+    return check_launch("lcp_moments");
+}
+
+extern "C" lcp_status lcp_surrogate_features(const float* mom, int H, int W, double dx, double dy, const float* iso,
+                                             int K, void* feat, float* prior, lcp_stream_t stream) {
+    if (H < 2 || W < 2) return fail(LCP_ERR_ARG, "lcp_surrogate_features: need H, W >= 2");
+    lcp_status s = check_spacing("lcp_surrogate_features", dx, dy);
+    if (s != LCP_OK) return s;
+    IsoParams ip;
+    if ((s = check_iso_host("lcp_surrogate_features", iso, K, ip)) != LCP_OK) return s;
+    if (!mom || !aligned16(mom) || !feat || !aligned16(feat))
+        return fail(LCP_ERR_ARG, "lcp_surrogate_features: mom and feat must be 16-byte aligned device arrays");
+    const int64_t cells = (int64_t)(H - 1) * (W - 1);
+    features_kernel<<<grid_for(cells, 256, 8), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const float4*>(mom), H, W, make_spacing(dx, dy), ip, (__nv_bfloat16*)feat, prior);
+    return check_launch("lcp_surrogate_features");
+}
+
+extern "C" lcp_status lcp_mlp_forward(const float* params, const void* feat, const float* prior, int64_t n, float* y,
+                                      lcp_stream_t stream) {
+    if (!params || !feat || !y || n < 1 || !aligned16(feat))
+        return fail(LCP_ERR_ARG, "lcp_mlp_forward: NULL/misaligned pointer or n < 1");
+    mlp_forward_kernel<<<grid_for(n, 64, 8), kMT, 0, (cudaStream_t)stream>>>(
+        params, (const __nv_bfloat16*)feat, prior, n, y);
+    return check_launch("lcp_mlp_forward");
+}
+
+extern "C" lcp_status lcp_mlp_backward(const float* params, const void* feat, const float* prior, const float* target,
+                                       int64_t n, float* grad, float* loss, lcp_stream_t stream) {
+    if (!params || !feat || !target || !grad || n < 1 || !aligned16(feat))
+        return fail(LCP_ERR_ARG, "lcp_mlp_backward: NULL/misaligned pointer or n < 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    static std::mutex mu;
+    static bool set[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return fail(LCP_ERR_CUDA, "lcp_mlp_backward: no usable current device");
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!set[dev]) {
+            if (cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(BwdSmem)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(LCP_ERR_CUDA, "lcp_mlp_backward: %zu bytes of shared memory not available", sizeof(BwdSmem));
+            }
+            set[dev] = true;
+        }
+    }
+    if (cudaMemsetAsync(grad, 0, LCP_MLP_NPARAMS * sizeof(float), st) != cudaSuccess ||
+        (loss && cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess)) {
+        cudaGetLastError();
+        return fail(LCP_ERR_CUDA, "lcp_mlp_backward: clearing the outputs failed");
+    }
+    mlp_backward_kernel<<<grid_for(n, 64, 2), kMT, sizeof(BwdSmem), st>>>(
+        params, (const __nv_bfloat16*)feat, prior, target, n, grad, loss);
+    return check_launch("lcp_mlp_backward");
+}
+
+extern "C" lcp_status lcp_adam_step(float* params, const float* grad, float* m, float* v, int64_t n, int t, float lr,
+                                    float beta1, float beta2, float eps, lcp_stream_t stream) {
+    if (!params || !grad || !m || !v || n < 1 || t < 1)
+        return fail(LCP_ERR_ARG, "lcp_adam_step: NULL pointer, n < 1 or t < 1");
+    if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps >= 0.f))
+        return fail(LCP_ERR_ARG, "lcp_adam_step: need 0 <= beta < 1 and eps >= 0");
+    const float c1 = (float)(1.0 / (1.0 - std::pow((double)beta1, (double)t)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow((double)beta2, (double)t)));
+    adam_kernel<<<grid_for(n, 256, 4), 256, 0, (cudaStream_t)stream>>>(params, grad, m, v, n, lr, beta1, beta2, eps,
+                                                                        c1, c2);
+    return check_launch("lcp_adam_step");
+}
+
+extern "C" lcp_status lcp_mlp_infer(const float* mom, int H, int W, double dx, double dy, const float* iso, int K,
+                                    const float* params, void* lcp_out, lcp_dtype out_dtype, lcp_stream_t stream) {
+    if (H < 2 || W < 2) return fail(LCP_ERR_ARG, "lcp_mlp_infer: need H, W >= 2");
+    lcp_status s = check_spacing("lcp_mlp_infer", dx, dy);
+    if (s != LCP_OK) return s;
+    IsoParams ip;
+    if ((s = check_iso_host("lcp_mlp_infer", iso, K, ip)) != LCP_OK) return s;
+    if (!mom || !aligned16(mom) || !params || !lcp_out)
+        return fail(LCP_ERR_ARG, "lcp_mlp_infer: NULL or misaligned pointer");
+    if (out_dtype != LCP_F32 && out_dtype != LCP_F16) return fail(LCP_ERR_ARG, "lcp_mlp_infer: out dtype must be F32 or F16");
+    const dim3 grid((W - 1 + kIC - 1) / kIC, (H - 1 + kIR - 1) / kIR);
+    if (grid.y > 65535) return fail(LCP_ERR_UNSUPPORTED, "lcp_mlp_infer: H too large");
+    const float4* m4 = reinterpret_cast<const float4*>(mom);
+    const Spacing sp = make_spacing(dx, dy);
+    if (out_dtype == LCP_F16)
+        mlp_infer_kernel<__half><<<grid, kMT, 0, (cudaStream_t)stream>>>(m4, H, W, sp, ip, params, (__half*)lcp_out);
+    else
+        mlp_infer_kernel<float><<<grid, kMT, 0, (cudaStream_t)stream>>>(m4, H, W, sp, ip, params, (float*)lcp_out);
+    return check_launch("lcp_mlp_infer");
+}

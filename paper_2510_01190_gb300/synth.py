@@ -366,10 +366,12 @@ def fourier_batch_torch(descs, k: int = 16, device="cuda", dtype=None, n_modes: 
     return fields
 
 
-def mlp_init_params(seed: int = 0, n_in: int = 17, hidden: int = 64):
+def mlp_init_params(seed: int = 0, n_in: int = 17, hidden: int = 64, zero_output: bool = False):
     """Initial weights of the 17 -> 64 -> 64 -> 1 surrogate network: Glorot-
-    uniform matrices (bound sqrt(6 / (fan_in + fan_out))), zero biases.
-    Layout as the network is written, x @ W: W1 [17, 64], W2 [64, 64], w3 [64].
+    uniform matrices (bound sqrt(6 / (fan_in + fan_out))), zero biases;
+    ``zero_output`` sets the output weights to 0 as well (a network that starts
+    as its prior).  Layout as the network is written, x @ W: W1 [17, 64],
+    W2 [64, 64], w3 [64].
 
     returns dict of float32 arrays (b3 a 0-d array)
     """
@@ -379,6 +381,9 @@ def mlp_init_params(seed: int = 0, n_in: int = 17, hidden: int = 64):
         lim = math.sqrt(6.0 / (a + b))
         return g.uniform(-lim, lim, shape).astype(np.float32)
 
-    return dict(W1=glorot(n_in, hidden, (n_in, hidden)), b1=np.zeros(hidden, np.float32),
-                W2=glorot(hidden, hidden, (hidden, hidden)), b2=np.zeros(hidden, np.float32),
-                w3=glorot(hidden, 1, (hidden,)), b3=np.zeros((), np.float32))
+    p = dict(W1=glorot(n_in, hidden, (n_in, hidden)), b1=np.zeros(hidden, np.float32),
+             W2=glorot(hidden, hidden, (hidden, hidden)), b2=np.zeros(hidden, np.float32),
+             w3=glorot(hidden, 1, (hidden,)), b3=np.zeros((), np.float32))
+    if zero_output:
+        p["w3"][:] = 0.0
+    return p

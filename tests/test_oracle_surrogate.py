@@ -123,6 +123,22 @@ def test_mlp_forward_hand_evaluated():
     want = 1.0 / (1.0 + math.exp(-(2.5 * h2 + 0.7)))
     y, _ = S.mlp_forward(one, x)
     assert y[0] == pytest.approx(want, abs=1e-15)
+    # the prior adds to the output's pre-activation; a zero output layer returns sigmoid(prior)
+    y, _ = S.mlp_forward(one, x, prior=np.array([-1.25]))
+    assert y[0] == pytest.approx(1.0 / (1.0 + math.exp(-(2.5 * h2 + 0.7 - 1.25))), abs=1e-15)
+    y, _ = S.mlp_forward(zero | {"b3": np.asarray(0.0)}, np.ones((1, 17)), prior=np.array([2.0]))
+    assert y[0] == pytest.approx(1.0 / (1.0 + math.exp(-2.0)), abs=1e-15)
+
+
+def test_prior_is_the_closed_form_logit():
+    kap = np.zeros((4, 3, 3))
+    kap[0] = np.arange(9).reshape(3, 3) * 0.1
+    kap[1] = 0.04
+    f = S.surrogate_features(kap, [0.25, 5.0])
+    pr = S.surrogate_prior(f)
+    g = np.clip(f[..., 16], 1e-6, 1 - 1e-6)
+    assert np.allclose(1.0 / (1.0 + np.exp(-pr)), g, rtol=1e-12, atol=1e-15)
+    assert np.all(pr[1] == pytest.approx(math.log(1e-6 / (1 - 1e-6))))  # c far above: LCP 0, clamped
 
 
 def test_mlp_backward_matches_finite_differences():
@@ -130,7 +146,8 @@ def test_mlp_backward_matches_finite_differences():
     g = np.random.Generator(np.random.PCG64(7))
     x = g.normal(0, 1, (20, 17))
     t = g.uniform(0, 1, 20)
-    y, cache = S.mlp_forward(p, x)
+    prior = g.normal(0, 2, 20)
+    y, cache = S.mlp_forward(p, x, prior)
     grads = S.mlp_backward(p, cache, t)
     eps = 1e-6
     for k in p:
@@ -140,9 +157,9 @@ def test_mlp_backward_matches_finite_differences():
             q = {kk: np.array(vv, copy=True) for kk, vv in p.items()}
             fq = q[k].reshape(-1)
             fq[idx] += eps
-            lp = S.mse_loss(S.mlp_forward(q, x)[0], t)
+            lp = S.mse_loss(S.mlp_forward(q, x, prior)[0], t)
             fq[idx] -= 2 * eps
-            lm = S.mse_loss(S.mlp_forward(q, x)[0], t)
+            lm = S.mse_loss(S.mlp_forward(q, x, prior)[0], t)
             fd = (lp - lm) / (2 * eps)
             assert gk[idx] == pytest.approx(fd, rel=1e-5, abs=1e-10), (k, idx)
 
