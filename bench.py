@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-mc", action="store_true", help="skip the Monte Carlo equal-error comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--workload", choices=["latlon", "batch", "learned"], default="latlon",
+    ap.add_argument("--workload", choices=["latlon", "batch", "learned", "ocean"], default="latlon",
                     help="latlon: the 721x1440 field (default); batch: 256 uneven fields in one persistent launch")
     ap.add_argument("--tile", type=str, default=None,
                     help="batch workload: force the tile shape ROWS,COLS instead of autotuning")
@@ -721,6 +721,117 @@ def learned_arm(args):
     return 0
 
 
+def ws_row_bands(h: int, w: int) -> int:
+    """Row bands of lcp_fused_ws for an h x w grid (one statistics and, for
+    K <= 32, one LCP launch each): bands of record rows that fit a 48 MB
+    budget (two 16-byte records per vertex, 3 halo rows), in multiples of the
+    LCP kernel's 8-row tiles."""
+    rows = (48 << 20) // (2 * w * 16) - 2
+    rows = max(rows, 8)
+    if rows >= h - 1:
+        return 1
+    band = (rows // 8) * 8
+    return -(-(h - 1) // band)
+
+
+OCEAN_WORKLOAD = ("ocean 8192x8192, 20 members bf16 (5000 Gaussian eddies + noise 0.05), 4 isovalues; "
+                  "fused closed-form LCP (fp32 maps)")
+
+
+def ocean_arm(args):
+    """Config-4 workload: 8192^2 bf16 members through lcp_fused_ws, fp32 maps."""
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = False
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = True
+    import paper_2510_01190_gb300 as lib
+    from paper_2510_01190_gb300 import synth
+
+    lib.load()
+    d = synth.eddy_ensemble_torch(0, device=dev)
+    u, v, iso = d["u"], d["v"], d["isovalues"]
+    Mm, Hh, Ww = u.shape
+    Kk, Hc, Wc = len(iso), Hh - 1, Ww - 1
+    out = torch.empty((Kk, Hc, Wc), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        lib.lcp_fused_ws(u, v, iso, 1.0, 1.0, 1, out=out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local).start()
+    time.sleep(0.35)
+    n = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    if pg:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    for i in range(n):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if pg:
+        torch.distributed.barrier()
+    time.sleep(0.25)
+    clocks.stop()
+    total_ms = max_over_ranks(ev[0][0].elapsed_time(ev[-1][1]), device=dev)
+    kern_ms = sum(a.elapsed_time(b) for a, b in ev) / n
+    ms_per_step = total_ms / n
+    value = weak_scaling_value(Hc * Wc, world, ms_per_step)
+    alg = 2 * Mm * Hh * Ww * 2 + Kk * Hc * Wc * 4
+    peak, peak_kind = measured_hbm_peak()
+    achieved = alg / (kern_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+            "kernel": "lcp_fused_ws step: stats_ws_kernel<bf16,8> + lcp_rows_kernel<4,nomask,float> per row band",
+            "alg_bytes_per_launch": alg, "kernel_ms": round(kern_ms, 4)}
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        import oracle as O
+
+        rows, cells, nb, t0 = 33, 0, 0, time.perf_counter()
+        while time.perf_counter() - t0 < 12.0:
+            j0 = (nb * 977) % (Hh - rows)
+            O.lcp_closed_form(u[:, j0:j0 + rows, :2048].float().cpu().numpy(),
+                              v[:, j0:j0 + rows, :2048].float().cpu().numpy(), 1.0, 1.0, iso)
+            cells += (rows - 1) * 2047
+            nb += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nb} bands of {rows} rows x 2048 cols x {Mm} members, K={Kk} (FP64 numpy, single thread)",
+               "seconds": round(dt, 2)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 members, f32 arithmetic", "data": "synthetic",
+            "config": {"workload": OCEAN_WORKLOAD, "H": Hh, "W": Ww, "M": Mm, "K": Kk, "global_batch": world,
+                       "parallelism": f"independent fields x{world}" if world > 1 else "single",
+                       "l2": "no flush: inputs 5.4 GB > 129 MB L2", "lcp_values_per_s": value * Kk,
+                       "hbm_frac_of_measured": roof["frac"]},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": None,
+            "e2e_note": "not measured for this line: 5.4 GB of members per step would be pinned on the host",
+            "clocks": clocks.summary(t_wall0, t_wall1), "gpu_launches": 2 * ws_row_bands(Hh, Ww) * n,
+            "gpu": torch.cuda.get_device_name(dev),
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -729,6 +840,8 @@ def main():
         return batch_arm(args)
     if args.workload == "learned":
         return learned_arm(args)
+    if args.workload == "ocean":
+        return ocean_arm(args)
     return our_arm(args)
 
 

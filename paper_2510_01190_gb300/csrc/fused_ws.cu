@@ -34,6 +34,7 @@
 // Grids whose records would not fit comfortably in L2 are processed in bands
 // of rows (records of the band plus one halo row on each side, then its
 // cells), so the workspace never spills to HBM.
+#include <cstdlib>
 #include <mutex>
 
 #include "lcp_common.cuh"
@@ -309,6 +310,8 @@ __global__ void __launch_bounds__(kRT, KX <= 4 ? 3 : (KX <= 16 ? 2 : 1))
         }
         __syncthreads();
     }
+    // the next isovalue pass may launch once every block of this grid is past its wait
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const bool last_warp = warp == kRT / 32 - 1;
     const int i = c0 + t, ic = min(i, W - 1);
     const bool ok = i < Wc;
@@ -443,6 +446,175 @@ __global__ void __launch_bounds__(kRT, KX <= 4 ? 3 : (KX <= 16 ? 2 : 1))
     }
 }
 
+// Barrier-free variant: every warp evaluates 32 cells on its own.  Lane l owns
+// vertex c0w + l; the right neighbour's (P(D<c), P(D>=c)) and class bits come
+// from lane l + 1 by shuffle, and for lane 31 from the warp's 33rd vertex,
+// whose isovalues are evaluated one per lane (lane k: isovalue k) and passed
+// on by shuffle.  No shared memory, no barriers after the dependency wait;
+// 32-cell warps keep the mask words aligned.  KX <= 8 isovalues per pass.
+constexpr int kWT = 128;  // threads (4 warps = 128 cells) per block
+
+template <int KX, bool MASK, typename OutT>
+__global__ void __launch_bounds__(kWT, 4)
+    lcp_warp_rows_kernel(const __grid_constant__ RowsParams p, const __grid_constant__ IsoParams iso) {
+    static_assert(KX >= 1 && KX <= 8, "isovalues per pass");
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int H = p.H, W = p.W, Hc = H - 1, Wc = W - 1;
+    const int c0w = blockIdx.x * kWT + warp * 32;
+    const int a = p.r_begin + blockIdx.y * kTR;
+    if (a >= p.r_end) return;
+    const int e = min(a + kTR, p.r_end);  // cells [a, e), vertex rows a..e
+    if (p.dep) {  // wait (bounded) until the statistics rows this band reads are complete
+        if (t == 0) {
+            int blo, bhi;
+            band_blocks(p.n_begin, p.sv, W, H, p.r_begin, p.r_end, blockIdx.y, blo, bhi);
+            const uint32_t need = (uint32_t)(bhi - blo + 1);
+            const long long t0 = clock64();
+            while (ld_acquire(&p.dep[blockIdx.y]) < need) {
+                if (clock64() - t0 > kWaitBudget) {
+                    atomicOr(&g_ws_status, 1u);
+                    break;
+                }
+                __nanosleep(200);
+            }
+        }
+        __syncthreads();
+    }
+    // the next isovalue pass may launch once every block of this grid is past its wait
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (c0w >= Wc) return;  // whole warp beyond the last cell (uniform per warp)
+    const int i = c0w + lane, ic = min(i, W - 1);
+    const bool ok = i < Wc;
+    const bool osx = ic == 0 || ic == W - 1;
+    const float sx = osx ? p.sp.sx1 : p.sp.sx2, sxq = osx ? p.sp.sx1q : p.sp.sx2q;
+    const bool edge_lane = lane == 0 || lane == 31;
+    const int iedge = lane == 0 ? max(ic - 1, 0) : min(ic + 1, W - 1);
+    const int ix = min(c0w + 32, W - 1);  // the warp's 33rd vertex (lane 0 loads its records)
+    const bool osxx = ix == 0 || ix == W - 1;
+    const float sx_x = osxx ? p.sp.sx1 : p.sp.sx2, sxq_x = osxx ? p.sp.sx1q : p.sp.sx2q;
+    const int ixl = max(ix - 1, 0), ixr = min(ix + 1, W - 1);
+    const int wi = c0w >> 5;
+    float c[KX];
+#pragma unroll
+    for (int k = 0; k < KX; ++k) c[k] = iso.c[k];
+    float cl = 0.0f;  // this lane's isovalue for the 33rd vertex
+#pragma unroll
+    for (int k = 0; k < KX; ++k)
+        if (k == lane) cl = c[k];
+
+    const float4* up = p.st + (int64_t)(a - p.row0) * W;  // u records of the current row
+    const float4* vpl = p.st + p.ps;
+    auto vrow = [&](int j) { return vpl + (int64_t)(j - p.row0) * W; };
+    float4 U = ld_rec(up + ic), UE = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (edge_lane) UE = ld_rec(up + iedge);
+    float4 VM = ld_rec(vrow(max(a - 1, 0)) + ic), V0 = ld_rec(vrow(a) + ic), VP = ld_rec(vrow(min(a + 1, H - 1)) + ic);
+    // 33rd vertex records (lane 0): u at ix-1, ix+1; v at (j-1, ix), (j+1, ix)
+    float4 XL = make_float4(0.f, 0.f, 0.f, 0.f), XR = XL, XD = XL, XU = XL;
+    if (lane == 0) {
+        XL = ld_rec(up + ixl);
+        XR = ld_rec(up + ixr);
+        XD = ld_rec(vrow(max(a - 1, 0)) + ix);
+        XU = ld_rec(vrow(min(a + 1, H - 1)) + ix);
+    }
+    float ph_prev[KX], qh_prev[KX];
+    uint32_t b_prev = 0, bn_prev = 0;
+    const int64_t plane = (int64_t)Hc * Wc, mplane = (int64_t)Hc * p.n_words;
+    OutT* po = reinterpret_cast<OutT*>(p.out) + (int64_t)p.kbase * plane + (int64_t)(a - 1) * Wc + i;
+    uint32_t* pm = MASK ? p.mask + ((int64_t)p.kbase * Hc + (a - 1)) * p.n_words + wi : nullptr;
+    for (int j = a; j <= e; ++j) {
+        const float4 Uc = U, UEc = UE, XLc = XL, XRc = XR, XDc = XD, XUc = XU;
+        float4 Vn = VP;
+        if (j < e) {  // next row in flight while this one is evaluated
+            up += W;
+            U = ld_rec(up + ic);
+            if (edge_lane) UE = ld_rec(up + iedge);
+            Vn = ld_rec(vrow(min(j + 2, H - 1)) + ic);
+            if (lane == 0) {
+                XL = ld_rec(up + ixl);
+                XR = ld_rec(up + ixr);
+                XD = ld_rec(vrow(j) + ix);
+                XU = ld_rec(vrow(min(j + 2, H - 1)) + ix);
+            }
+        }
+        const bool osy = j == 0 || j == H - 1;
+        const float sy = osy ? p.sp.sy1 : p.sp.sy2, syq = osy ? p.sp.sy1q : p.sp.sy2q;
+        // own vertex (Eqs. 2/3, one-sided at the edges)
+        float4 L = make_float4(__shfl_up_sync(0xFFFFFFFFu, Uc.x, 1), __shfl_up_sync(0xFFFFFFFFu, Uc.y, 1),
+                               __shfl_up_sync(0xFFFFFFFFu, Uc.z, 1), 0.f);
+        float4 R = make_float4(__shfl_down_sync(0xFFFFFFFFu, Uc.x, 1), __shfl_down_sync(0xFFFFFFFFu, Uc.y, 1),
+                               __shfl_down_sync(0xFFFFFFFFu, Uc.z, 1), 0.f);
+        if (lane == 0) L = UEc;
+        if (lane == 31) R = UEc;
+        if (ic == 0) L = Uc;
+        if (ic == W - 1) R = Uc;
+        const float4 Vlo = j > 0 ? VM : V0;
+        const float4 Vhi = j < H - 1 ? VP : V0;
+        const float mu = fmaf((R.x - L.x) + (R.y - L.y), sx, ((Vhi.x - Vlo.x) + (Vhi.y - Vlo.y)) * sy);
+        const float var = fmaf(R.z + L.z, sxq, (Vhi.z + Vlo.z) * syq);
+        // 33rd vertex on lane 0, then to every lane
+        float mux = 0.f, varx = 0.f;
+        if (lane == 0) {
+            // (ixl, ixr) and the clamped rows already are the one-sided stencil at the edges
+            mux = fmaf((XRc.x - XLc.x) + (XRc.y - XLc.y), sx_x, ((XUc.x - XDc.x) + (XUc.y - XDc.y)) * sy);
+            varx = fmaf(XRc.z + XLc.z, sxq_x, (XUc.z + XDc.z) * syq);
+        }
+        mux = __shfl_sync(0xFFFFFFFFu, mux, 0);
+        varx = __shfl_sync(0xFFFFFFFFu, varx, 0);
+        const bool zero = var == 0.0f;
+        const float s = rsqrtf(2.0f * var);
+        float2 pq[KX];
+        uint32_t b = 0;
+        if constexpr (KX == 1) {
+            const bool below = mu < c[0];
+            pq[0] = vertex_pq(mu, s, zero, c[0], below);
+            b = below;
+        } else {
+#pragma unroll
+            for (int k = 0; k < KX; k += 2) {
+                const bool b0 = mu < c[k], b1 = mu < c[k + 1];
+                vertex_pq2(mu, s, zero, make_float2(c[k], c[k + 1]), b0, b1, pq[k], pq[k + 1]);
+                b |= ((uint32_t)b0 << k) | ((uint32_t)b1 << (k + 1));
+            }
+        }
+        const bool belowx = mux < cl;
+        const float2 pqx = vertex_pq(mux, rsqrtf(2.0f * varx), varx == 0.0f, cl, belowx);
+        const uint32_t bx = __ballot_sync(0xFFFFFFFFu, lane < KX && belowx);
+        uint32_t bn = __shfl_down_sync(0xFFFFFFFFu, b, 1);
+        if (lane == 31) bn = bx;
+        const uint32_t cross = ok ? ((b_prev | bn_prev | b | bn) & ~(b_prev & bn_prev & b & bn)) : 0u;
+        if (j > a) {
+            po += Wc;
+            if (MASK) pm += p.n_words;
+        }
+        OutT* o = po;
+        uint32_t* m = pm;
+#pragma unroll
+        for (int k = 0; k < KX; ++k) {
+            float2 nb = make_float2(__shfl_down_sync(0xFFFFFFFFu, pq[k].x, 1), __shfl_down_sync(0xFFFFFFFFu, pq[k].y, 1));
+            const float2 xk = make_float2(__shfl_sync(0xFFFFFFFFu, pqx.x, k), __shfl_sync(0xFFFFFFFFu, pqx.y, k));
+            if (lane == 31) nb = xk;
+            const float2 h = __fmul2_rn(pq[k], nb);  // (p_i p_i+1, q_i q_i+1) of this vertex row
+            if (j > a) {
+                const float lcp = fmaf(-qh_prev[k], h.y, fmaf(-ph_prev[k], h.x, 1.0f));
+                if (ok) *o = to_out<OutT>(clamp01_nan(lcp));
+                o += plane;
+                if (MASK) {
+                    const uint32_t word = __ballot_sync(0xFFFFFFFFu, (cross >> k) & 1u);
+                    if (lane == 0 && wi < p.n_words) *m = word;
+                    m += mplane;
+                }
+            }
+            ph_prev[k] = h.x;
+            qh_prev[k] = h.y;
+        }
+        b_prev = b;
+        bn_prev = bn;
+        VM = V0;
+        V0 = VP;
+        VP = Vn;
+    }
+}
+
 // ---- host ----------------------------------------------------------------------
 struct Layout {
     int band_rows;       // cell rows per band
@@ -509,8 +681,43 @@ lcp_status launch_rows_k(const RowsParams& p, const IsoParams& ip, cudaStream_t 
     return LCP_OK;
 }
 
+template <int KX, bool MASK, typename OutT>
+lcp_status launch_warp_rows_k(const RowsParams& p, const IsoParams& ip, cudaStream_t st, bool pdl) {
+    const int rows = p.r_end - p.r_begin;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.W - 1 + kWT - 1) / kWT, (rows + kTR - 1) / kTR);
+    cfg.blockDim = dim3(kWT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (pdl) {
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, lcp_warp_rows_kernel<KX, MASK, OutT>, p, ip);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LCP_ERR_CUDA, "lcp_fused_ws: LCP kernel launch failed: %s", cudaGetErrorString(e));
+    }
+    return LCP_OK;
+}
+
+// Up to 8 isovalues: the barrier-free warp kernel (one pass).  More: the
+// shared-memory kernel in passes of up to 32, whose single pass over the
+// records beats several warp-kernel passes.
 template <bool MASK, typename OutT>
-lcp_status launch_rows_chunk(const RowsParams& p, const IsoParams& ip, cudaStream_t st, bool pdl) {
+lcp_status launch_rows_chunk(const RowsParams& p, const IsoParams& ip, cudaStream_t st, bool pdl, bool warp_rows) {
+    if (warp_rows) {
+        switch (ip.K) {
+            case 1: return launch_warp_rows_k<1, MASK, OutT>(p, ip, st, pdl);
+            case 2: return launch_warp_rows_k<2, MASK, OutT>(p, ip, st, pdl);
+            case 4: return launch_warp_rows_k<4, MASK, OutT>(p, ip, st, pdl);
+            case 8: return launch_warp_rows_k<8, MASK, OutT>(p, ip, st, pdl);
+        }
+        return fail(LCP_ERR_UNSUPPORTED, "lcp_fused_ws: isovalue chunk %d", ip.K);
+    }
     switch (ip.K) {
         case 1: return launch_rows_k<1, MASK, OutT>(p, ip, st, pdl);
         case 2: return launch_rows_k<2, MASK, OutT>(p, ip, st, pdl);
@@ -528,19 +735,21 @@ template <typename OutT>
 lcp_status launch_rows(const RowsParams& p0, const float* iso, int K, cudaStream_t st) {
     RowsParams p = p0;
     int kb = 0;
-    bool first = true;
+    const bool warp_rows = K <= 8;
+    const int max_chunk = warp_rows ? 8 : kMaxKPass;
     while (kb < K) {
-        int chunk = 32;
+        int chunk = max_chunk;
         while (chunk > K - kb) chunk >>= 1;
         IsoParams ip;
         ip.K = chunk;
         for (int k = 0; k < chunk; ++k) ip.c[k] = iso[kb + k];
         p.kbase = kb;
-        const lcp_status s = p.mask ? launch_rows_chunk<true, OutT>(p, ip, st, first)
-                                    : launch_rows_chunk<false, OutT>(p, ip, st, first);
+        // every pass is a programmatic dependent of the kernel before it: each
+        // waits on the counters of its rows, not on stream order
+        const lcp_status s = p.mask ? launch_rows_chunk<true, OutT>(p, ip, st, true, warp_rows)
+                                    : launch_rows_chunk<false, OutT>(p, ip, st, true, warp_rows);
         if (s != LCP_OK) return s;
         kb += chunk;
-        first = false;
     }
     return LCP_OK;
 }

@@ -373,3 +373,34 @@ def test_fused_ws_row_bands_match_oracle(lib):
     assert np.max(np.abs(_np(lcp) - ref["lcp"])) <= LCP_TOL
     guard = _oracle_mask_guard(ref["mu_d"], iso)
     assert np.array_equal(lib.unpack_mask(mask, w).cpu().numpy()[guard], ref["mask"][guard])
+
+
+@pytest.mark.slow
+def test_fused_ws_ocean_8192_bf16_sampled(lib):
+    """The 8192 x 8192 ocean-shaped workload (20 bf16 members, K = 4: 5.4 GB of
+    members) in the bench's launch configuration; the oracle evaluates vertex
+    crops (corner, interior, far edge) on the same bf16-rounded values, and the
+    cells whose stencils lie inside a crop are compared."""
+    if torch.cuda.get_device_properties(0).total_memory < 60e9:
+        pytest.skip("needs the full-size device memory")
+    d = synth.eddy_ensemble_torch(0)
+    u, v, iso = d["u"], d["v"], d["isovalues"]
+    H, W = u.shape[1:]
+    lcp, mask = lib.lcp_fused_ws(u, v, iso, 1.0, 1.0, 1, mask=True)
+    torch.cuda.synchronize()
+    for (y0, x0) in ((0, 0), (4000, 3001), (H - 70, W - 110)):
+        y1, x1 = min(y0 + 70, H), min(x0 + 110, W)
+        uc, vc = _np(u[:, y0:y1, x0:x1]), _np(v[:, y0:y1, x0:x1])
+        ref = O.lcp_closed_form(uc, vc, 1.0, 1.0, iso)
+        vy = np.ones(y1 - y0, bool)
+        vx = np.ones(x1 - x0, bool)
+        vy[0], vy[-1] = y0 == 0, y1 == H
+        vx[0], vx[-1] = x0 == 0, x1 == W
+        sel = (vy[:-1] & vy[1:])[:, None] & (vx[:-1] & vx[1:])[None, :]
+        got = _np(lcp[:, y0:y1 - 1, x0:x1 - 1])
+        assert np.max(np.abs(got - ref["lcp"])[:, sel]) <= LCP_TOL
+        guard = _oracle_mask_guard(ref["mu_d"], iso) & sel[None]
+        gm = lib.unpack_mask(mask[:, y0:y1 - 1], W).cpu().numpy()[:, :, x0:x1 - 1]
+        assert np.array_equal(gm[guard], ref["mask"][guard])
+    del u, v, lcp, mask, d
+    torch.cuda.empty_cache()
