@@ -112,6 +112,24 @@ struct SLoad<float, 4> {
     static __device__ __forceinline__ raw_t load(const float* p, uint64_t pol) { return ld_stream_f4(p, pol); }
     static __device__ __forceinline__ void cvt(const raw_t& r, float* x) { x[0] = r.x; x[1] = r.y; x[2] = r.z; x[3] = r.w; }
 };
+__device__ __forceinline__ uint2 ld_stream_u2(const void* p, uint64_t pol) {
+    uint2 r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+                 : "=r"(r.x), "=r"(r.y)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+template <>
+struct SLoad<__nv_bfloat16, 4> {
+    using raw_t = uint2;
+    static __device__ __forceinline__ raw_t load(const __nv_bfloat16* p, uint64_t pol) { return ld_stream_u2(p, pol); }
+    static __device__ __forceinline__ void cvt(const raw_t& r, float* x) {
+        x[0] = __uint_as_float(r.x << 16);
+        x[1] = __uint_as_float(r.x & 0xFFFF0000u);
+        x[2] = __uint_as_float(r.y << 16);
+        x[3] = __uint_as_float(r.y & 0xFFFF0000u);
+    }
+};
 template <>
 struct SLoad<__nv_bfloat16, 8> {
     using raw_t = uint4;
@@ -158,7 +176,7 @@ __device__ __forceinline__ void store_stats(const StatsWsParams& p, int64_t n, c
 }
 
 template <typename T, int VEC>
-__global__ void __launch_bounds__(kST) stats_ws_kernel(const __grid_constant__ StatsWsParams p) {
+__global__ void __launch_bounds__(kST, 4) stats_ws_kernel(const __grid_constant__ StatsWsParams p) {
     const T* __restrict__ u = reinterpret_cast<const T*>(p.u);
     const T* __restrict__ v = reinterpret_cast<const T*>(p.v);
     const uint64_t pol = policy_evict_first();
@@ -189,7 +207,7 @@ __global__ void __launch_bounds__(kST) stats_ws_kernel(const __grid_constant__ S
                     s2v[e] = fmaf(dv, dv, s2v[e]);
                 }
             };
-            constexpr int UNROLL = VEC >= 8 ? 4 : 8;
+            constexpr int UNROLL = VEC >= 8 ? 4 : 8;  // 16 loads in flight per thread
             int m = 1;
             for (; m + UNROLL <= M; m += UNROLL) {
                 typename L::raw_t ru[UNROLL], rv[UNROLL];
@@ -200,6 +218,19 @@ __global__ void __launch_bounds__(kST) stats_ws_kernel(const __grid_constant__ S
                 }
 #pragma unroll
                 for (int q = 0; q < UNROLL; ++q) acc(ru[q], rv[q]);
+            }
+            if (sizeof(typename L::raw_t) < 16 && m < M) {  // 8-byte loads: the remaining members as one batch
+                typename L::raw_t ru[UNROLL], rv[UNROLL];
+#pragma unroll
+                for (int q = 0; q < UNROLL; ++q)
+                    if (m + q < M) {
+                        ru[q] = L::load(u + (int64_t)(m + q) * p.stride + n0, pol);
+                        rv[q] = L::load(v + (int64_t)(m + q) * p.stride + n0, pol);
+                    }
+#pragma unroll
+                for (int q = 0; q < UNROLL; ++q)
+                    if (m + q < M) acc(ru[q], rv[q]);
+                m = M;
             }
             for (; m < M; ++m) acc(L::load(u + (int64_t)m * p.stride + n0, pol), L::load(v + (int64_t)m * p.stride + n0, pol));
             store_stats(p, n0, x0u, s1u, s2u, 0, keep, VEC);
@@ -861,6 +892,7 @@ extern "C" lcp_status lcp_fused_ws(const void* u, const void* v, lcp_dtype in_dt
     if (in_dtype == LCP_F32)
         return run<float, 4>(u, v, M, H, W, stride, ddof, dx, dy, iso, K, lcp_out, out_dtype, mask, workspace,
                              in16 && stride % 4 == 0, st);
-    return run<__nv_bfloat16, 8>(u, v, M, H, W, stride, ddof, dx, dy, iso, K, lcp_out, out_dtype, mask, workspace,
-                                 in16 && stride % 8 == 0, st);
+    const bool in8 = ((uintptr_t)u & 7) == 0 && ((uintptr_t)v & 7) == 0;
+    return run<__nv_bfloat16, 4>(u, v, M, H, W, stride, ddof, dx, dy, iso, K, lcp_out, out_dtype, mask, workspace,
+                                 in8 && stride % 4 == 0, st);
 }
