@@ -36,6 +36,7 @@
 // cells), so the workspace never spills to HBM.
 #include <cstdlib>
 #include <mutex>
+#include <type_traits>
 
 #include "lcp_common.cuh"
 
@@ -485,9 +486,11 @@ __global__ void __launch_bounds__(kRT, KX <= 4 ? 3 : (KX <= 16 ? 2 : 1))
 // 32-cell warps keep the mask words aligned.  KX <= 8 isovalues per pass.
 constexpr int kWT = 128;  // threads (4 warps = 128 cells) per block
 
-template <int KX, bool MASK, typename OutT>
+template <int KX, bool MASK, typename OutT, bool IDX32>
 __global__ void __launch_bounds__(kWT, 4)
     lcp_warp_rows_kernel(const __grid_constant__ RowsParams p, const __grid_constant__ IsoParams iso) {
+    // output and mask element offsets in 32 bits when the outputs fit (IDX32), else 64
+    using Off = typename std::conditional<IDX32, uint32_t, int64_t>::type;
     static_assert(KX >= 1 && KX <= 8, "isovalues per pass");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int H = p.H, W = p.W, Hc = H - 1, Wc = W - 1;
@@ -549,10 +552,14 @@ __global__ void __launch_bounds__(kWT, 4)
     }
     float ph_prev[KX], qh_prev[KX];
     uint32_t b_prev = 0, bn_prev = 0;
-    const int64_t plane = (int64_t)Hc * Wc, mplane = (int64_t)Hc * p.n_words;
-    OutT* po = reinterpret_cast<OutT*>(p.out) + (int64_t)p.kbase * plane + (int64_t)(a - 1) * Wc + i;
-    uint32_t* pm = MASK ? p.mask + ((int64_t)p.kbase * Hc + (a - 1)) * p.n_words + wi : nullptr;
-    for (int j = a; j <= e; ++j) {
+    const Off plane = (Off)Hc * (Off)Wc, mplane = (Off)Hc * (Off)p.n_words;
+    OutT* const obase = reinterpret_cast<OutT*>(p.out);
+    Off oo = (Off)p.kbase * plane + (Off)(a - 1) * (Off)Wc + (Off)i;  // row a - 1: advanced before the first store
+    Off mo = MASK ? ((Off)p.kbase * (Off)Hc + (Off)(a - 1)) * (Off)p.n_words + (Off)wi : (Off)0;
+#pragma unroll
+    for (int jj = 0; jj <= kTR; ++jj) {  // vertex rows a .. e (at most kTR + 1), unrolled: no window moves
+        const int j = a + jj;
+        if (j > e) break;
         const float4 Uc = U, UEc = UE, XLc = XL, XRc = XR, XDc = XD, XUc = XU;
         float4 Vn = VP;
         if (j < e) {  // next row in flight while this one is evaluated
@@ -614,11 +621,9 @@ __global__ void __launch_bounds__(kWT, 4)
         if (lane == 31) bn = bx;
         const uint32_t cross = ok ? ((b_prev | bn_prev | b | bn) & ~(b_prev & bn_prev & b & bn)) : 0u;
         if (j > a) {
-            po += Wc;
-            if (MASK) pm += p.n_words;
+            oo += (Off)Wc;
+            if (MASK) mo += (Off)p.n_words;
         }
-        OutT* o = po;
-        uint32_t* m = pm;
 #pragma unroll
         for (int k = 0; k < KX; ++k) {
             float2 nb = make_float2(__shfl_down_sync(0xFFFFFFFFu, pq[k].x, 1), __shfl_down_sync(0xFFFFFFFFu, pq[k].y, 1));
@@ -627,12 +632,10 @@ __global__ void __launch_bounds__(kWT, 4)
             const float2 h = __fmul2_rn(pq[k], nb);  // (p_i p_i+1, q_i q_i+1) of this vertex row
             if (j > a) {
                 const float lcp = fmaf(-qh_prev[k], h.y, fmaf(-ph_prev[k], h.x, 1.0f));
-                if (ok) *o = to_out<OutT>(clamp01_nan(lcp));
-                o += plane;
+                if (ok) obase[oo + (Off)k * plane] = to_out<OutT>(clamp01_nan(lcp));
                 if (MASK) {
                     const uint32_t word = __ballot_sync(0xFFFFFFFFu, (cross >> k) & 1u);
-                    if (lane == 0 && wi < p.n_words) *m = word;
-                    m += mplane;
+                    if (lane == 0 && wi < p.n_words) p.mask[mo + (Off)k * mplane] = word;
                 }
             }
             ph_prev[k] = h.x;
@@ -727,7 +730,12 @@ lcp_status launch_warp_rows_k(const RowsParams& p, const IsoParams& ip, cudaStre
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, lcp_warp_rows_kernel<KX, MASK, OutT>, p, ip);
+    // 32-bit offsets when every output element index of this pass fits
+    const int64_t n_out = (int64_t)(p.kbase + KX) * (p.H - 1) * (p.W - 1);
+    const int64_t n_mask = (int64_t)(p.kbase + KX) * (p.H - 1) * p.n_words;
+    const bool idx32 = n_out < (1ll << 31) && n_mask < (1ll << 31);
+    const cudaError_t e = idx32 ? cudaLaunchKernelEx(&cfg, lcp_warp_rows_kernel<KX, MASK, OutT, true>, p, ip)
+                                : cudaLaunchKernelEx(&cfg, lcp_warp_rows_kernel<KX, MASK, OutT, false>, p, ip);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(LCP_ERR_CUDA, "lcp_fused_ws: LCP kernel launch failed: %s", cudaGetErrorString(e));

@@ -11,6 +11,8 @@
 // so the C fragments of two adjacent 8-column tiles are exactly the A fragment
 // of the next layer's 16-wide k-step (no shared-memory round trip between
 // layers).
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstddef>
 #include <mutex>
@@ -115,7 +117,8 @@ __device__ __forceinline__ float4 vertex_cumulants(const float4* __restrict__ mu
 
 // Isovalue-independent part of a cell's features.
 struct CellPart {
-    float mu[4], sig[4], ratio[4], skew[4], kurt[4], var[4];
+    float mu[4], sig[4], inv_sig[4], ratio[4], skew[4], kurt[4];
+    VertexG g[4];  // the closed form's per-vertex scale (feature 16)
 };
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
@@ -126,8 +129,10 @@ __device__ __forceinline__ CellPart cell_part(const float4 (&k)[4]) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         p.mu[v] = k[v].x;
-        p.var[v] = fmaxf(k[v].y, 0.f);
-        p.sig[v] = sqrtf(p.var[v]);
+        const float var = fmaxf(k[v].y, 0.f);
+        p.sig[v] = sqrtf(var);
+        p.inv_sig[v] = p.sig[v] > 0.f ? 1.0f / p.sig[v] : 0.f;
+        p.g[v] = vertex_g(k[v].x, var);
         msum += p.sig[v];
     }
     const float mean_sig = 0.25f * msum;
@@ -154,9 +159,9 @@ __device__ __forceinline__ float prior_logit(float g) {
     return __logf(p) - __logf(1.0f - p);
 }
 
-// The 17 features of (cell, c), bf16, into a 32-wide row (16-byte aligned);
-// returns the prior (fp32).
-__device__ __forceinline__ float cell_features(const CellPart& p, float c, __nv_bfloat16* row) {
+// The 17 features of (cell, c) as 16 words of bf16 pairs (features 17..31
+// zero); returns the prior (fp32).
+__device__ __forceinline__ float cell_feature_words(const CellPart& p, float c, uint32_t (&w)[kFS / 2]) {
     float f[kFS];
 #pragma unroll
     for (int q = 0; q < kFS; ++q) f[q] = 0.f;
@@ -164,28 +169,32 @@ __device__ __forceinline__ float cell_features(const CellPart& p, float c, __nv_
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         const float d = c - p.mu[v];
-        f[4 * v + 0] = p.sig[v] > 0.f ? clampf(d / p.sig[v], -8.f, 8.f) : (d > 0.f ? 8.f : (d < 0.f ? -8.f : 0.f));
+        f[4 * v + 0] = p.sig[v] > 0.f ? clampf(d * p.inv_sig[v], -8.f, 8.f) : (d > 0.f ? 8.f : (d < 0.f ? -8.f : 0.f));
         f[4 * v + 1] = p.ratio[v];
         f[4 * v + 2] = p.skew[v];
         f[4 * v + 3] = p.kurt[v];
         float pv, qv;
-        below_above(p.mu[v], p.var[v], c, pv, qv);
+        below_above(p.g[v], c, pv, qv);
         pb *= pv;
         qb *= qv;
     }
     f[16] = 1.f - pb - qb;
-    uint4* out = reinterpret_cast<uint4*>(row);
 #pragma unroll
-    for (int q = 0; q < kFS / 8; ++q) {
-        uint32_t w[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(f[8 * q + 2 * e], f[8 * q + 2 * e + 1]);
-            w[e] = *reinterpret_cast<const uint32_t*>(&h);
-        }
-        out[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    for (int q = 0; q < kFS / 2; ++q) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
+        w[q] = *reinterpret_cast<const uint32_t*>(&h);
     }
     return prior_logit(f[16]);
+}
+
+// The features into a contiguous 32-wide bf16 row (16-byte aligned); returns the prior.
+__device__ __forceinline__ float cell_features(const CellPart& p, float c, __nv_bfloat16* row) {
+    uint32_t w[kFS / 2];
+    const float pr = cell_feature_words(p, c, w);
+    uint4* out = reinterpret_cast<uint4*>(row);
+#pragma unroll
+    for (int q = 0; q < kFS / 8; ++q) out[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    return pr;
 }
 
 __global__ void __launch_bounds__(256) features_kernel(const float4* __restrict__ mom, int H, int W, Spacing sp,
@@ -445,6 +454,250 @@ __global__ void __launch_bounds__(kMT) mlp_infer_kernel(const float4* __restrict
     }
     (void)ok;
 }
+
+// ---- 5b. fused inference on the 5th-generation tensor cores (tcgen05) ---------
+// Per CTA a block of 4 x 32 cells, as above; per isovalue its 128 feature rows
+// form one M = 128 tile.  Each thread owns one row (= one TMEM lane): it writes
+// the row's features into shared memory in the canonical K-major layout
+// (8-row x 16-byte core matrices), one elected thread issues the layer's
+// tcgen05.mma (K = 16 per instruction, FP32 accumulators in TMEM, operands
+// read through shared-memory descriptors) and commits to an mbarrier, and each
+// thread reads its row of the accumulators back with tcgen05.ld for the
+// epilogue (bias, tanh, the next layer's operand, and finally the output dot
+// product, prior and sigmoid).
+//
+// Shared-memory descriptor (64 bits): start address >> 4 in bits 0-13, leading
+// (K-direction) byte offset between core matrices >> 4 in bits 16-29, stride
+// (M/N-direction) byte offset between 8-row groups >> 4 in bits 32-45, the
+// descriptor version 1 in bits 46-47, no swizzle (bits 61-63 = 0).
+// Instruction descriptor (32 bits, kind::f16): D format F32 (bits 4-5 = 1), A
+// and B BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t kTmemCols = 64;  // D1, then D2 (D1 is read out before layer 2 is issued)
+constexpr long long kTcWaitBudget = 2000000000ll;  // clock cycles (~1 s) before an mbarrier wait gives up
+__device__ uint32_t g_sur_status = 0;
+
+struct TcSmem {
+    __align__(1024) __nv_bfloat16 W1[kHid * kFS];  // B operand of layer 1: N = 64 units x K = 32 features
+    __align__(1024) __nv_bfloat16 W2[kHid * kHid];  // B operand of layer 2: N = 64 x K = 64
+
+    // A operands: layer 1 (128 rows x 32 features, the first 8 KB) and then layer 2
+    // (128 rows x 64 units) in the same bytes: h1 is written after layer 1's
+    // MMAs have completed, the next features after layer 2's
+    __align__(1024) __nv_bfloat16 A[128 * kHid];
+    float4 kap[(kIR + 1) * (kIC + 1)];
+    float b1[kHid], b2[kHid], w3[kHid];
+    __align__(8) uint64_t mbar;
+    uint32_t tmem;
+    int abort_flag;  // set when an mbarrier wait gave up; read by all threads after a barrier
+};
+
+// Byte offset of element (row, k) in a K-major canonical tile with `kg` core
+// matrices along K: core matrix (row / 8, k / 8) at ((row / 8) kg + k / 8) 128.
+__host__ __device__ constexpr uint32_t canon_off(int row, int k, int kg) {
+    return (uint32_t)(((row >> 3) * kg + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+constexpr uint32_t kIdescM128N64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdescM128N64), "r"(accumulate));
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Bounded wait for the mbarrier phase `parity`; false (and the status bit) when
+// it gives up.  The clock is read every 64 tries.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    const long long t0 = clock64();
+    for (int it = 1;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63) == 0 && clock64() - t0 > kTcWaitBudget) {
+            atomicOr(&g_sur_status, 1u);
+            return false;
+        }
+    }
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ uint32_t tanh_bf16x2(float lo, float hi) {
+    uint32_t x = pack_bf16(lo, hi), y;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(x));
+    return y;
+}
+
+constexpr int kTcCtasPerSm = 5;
+
+template <typename OutT>
+__global__ void __launch_bounds__(kMT, kTcCtasPerSm) mlp_infer_tc_kernel(const float4* __restrict__ mom, int H, int W, Spacing sp,
+                                                             const __grid_constant__ IsoParams iso,
+                                                             const float* __restrict__ prm, OutT* __restrict__ out) {
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    // the dynamic window starts 16-byte aligned; round it up to 1024 for the tiles
+    TcSmem& S = *reinterpret_cast<TcSmem*>(tc_raw + ((1024 - (smem_addr(tc_raw) & 1023)) & 1023));
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // weights into the canonical layouts (bf16), vectors as fp32
+    for (int q = t; q < kHid * kFS; q += kMT) {
+        const int n = q / kFS, k = q - n * kFS;
+        *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(S.W1) + canon_off(n, k, kFS / 8)) =
+            __float2bfloat16_rn(k < 17 ? prm[kOffW1 + q] : 0.f);
+    }
+    for (int q = t; q < kHid * kHid; q += kMT) {
+        const int n = q >> 6, k = q & 63;
+        *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(S.W2) + canon_off(n, k, kHid / 8)) =
+            __float2bfloat16_rn(prm[kOffW2 + q]);
+    }
+    for (int q = t; q < kHid; q += kMT) {
+        S.b1[q] = prm[kOffB1 + q];
+        S.b2[q] = prm[kOffB2 + q];
+        S.w3[q] = prm[kOffW3 + q];
+    }
+    if (t == 0) {
+        S.abort_flag = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {  // TMEM: 64 FP32 columns x 128 lanes, the accumulator of either layer
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&S.tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    const int Hc = H - 1, Wc = W - 1;
+    const int64_t n_vert = (int64_t)H * W;
+    const uint32_t mbar = smem_addr(&S.mbar);
+    const uint32_t a0 = smem_addr(S.A), a1 = a0, w1 = smem_addr(S.W1), w2 = smem_addr(S.W2);
+    const float b3 = prm[kOffB3];
+    const int64_t plane = (int64_t)Hc * Wc;
+    const int nbx = (Wc + kIC - 1) / kIC, nblocks = nbx * ((Hc + kIR - 1) / kIR);
+    uint32_t phase = 0;
+    volatile int* abort_flag = &S.abort_flag;
+    tc_fence_before();
+    __syncthreads();  // TMEM address, mbarrier and weights are ready
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    // persistent: the CTA walks cell blocks of 4 x 32 cells
+    for (int blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+        const int a = (blk / nbx) * kIR, c0 = (blk % nbx) * kIC;
+        for (int q = t; q < (kIR + 1) * (kIC + 1); q += kMT) {
+            const int rr = q / (kIC + 1), cc = q - rr * (kIC + 1);
+            S.kap[q] = vertex_cumulants(mom, mom + n_vert, H, W, min(a + rr, H - 1), min(c0 + cc, W - 1), sp);
+        }
+        __syncthreads();
+        const int j = a + warp, i = c0 + lane;
+        float4 k4[4];
+        k4[0] = S.kap[warp * (kIC + 1) + lane];
+        k4[1] = S.kap[warp * (kIC + 1) + lane + 1];
+        k4[2] = S.kap[(warp + 1) * (kIC + 1) + lane];
+        k4[3] = S.kap[(warp + 1) * (kIC + 1) + lane + 1];
+        const CellPart part = cell_part(k4);
+        for (int q = 0; q < iso.K; ++q) {
+            // features of row t into A0
+            uint32_t fw[kFS / 2];
+            const float pr = cell_feature_words(part, iso.c[q], fw);
+#pragma unroll
+            for (int g = 0; g < kFS / 8; ++g)
+                *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(S.A) + canon_off(t, 8 * g, kFS / 8)) =
+                    make_uint4(fw[4 * g], fw[4 * g + 1], fw[4 * g + 2], fw[4 * g + 3]);
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (*abort_flag) break;  // uniform: read after the barrier, written only before one
+            if (t == 0) {  // layer 1: D1 = A0 W1^T (K = 32 in two steps)
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+                    tc_mma(tmem, smem_desc(a0 + 256 * s, 128, 512), smem_desc(w1 + 256 * s, 128, 512), s);
+                tc_commit(mbar);
+            }
+            if (!mbar_wait(mbar, phase)) *abort_flag = 1;
+            phase ^= 1u;
+            tc_fence_after();
+            // h1 = tanh(D1 + b1) as bf16 into A1
+#pragma unroll
+            for (int cg = 0; cg < 4; ++cg) {
+                float z[16];
+                tmem_ld16(lane_base + 16 * cg, z);
+                uint32_t hw[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    hw[e] = tanh_bf16x2(z[2 * e] + S.b1[16 * cg + 2 * e], z[2 * e + 1] + S.b1[16 * cg + 2 * e + 1]);
+                *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(S.A) + canon_off(t, 16 * cg, kHid / 8)) =
+                    make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(S.A) + canon_off(t, 16 * cg + 8, kHid / 8)) =
+                    make_uint4(hw[4], hw[5], hw[6], hw[7]);
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (*abort_flag) break;
+            if (t == 0) {  // layer 2: D2 = A1 W2^T (K = 64 in four steps)
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    tc_mma(tmem, smem_desc(a1 + 256 * s, 128, 1024), smem_desc(w2 + 256 * s, 128, 1024), s);
+                tc_commit(mbar);
+            }
+            if (!mbar_wait(mbar, phase)) *abort_flag = 1;
+            phase ^= 1u;
+            tc_fence_after();
+            // output: b3 + prior + w3 . tanh(D2), the tanh two units at a time (bf16x2), the dot product in fp32
+            float z3 = b3 + pr;
+#pragma unroll
+            for (int cg = 0; cg < 4; ++cg) {
+                float z[16];
+                tmem_ld16(lane_base + 16 * cg, z);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float2 h = unpack_bf16(
+                        tanh_bf16x2(z[2 * e] + S.b2[16 * cg + 2 * e], z[2 * e + 1] + S.b2[16 * cg + 2 * e + 1]));
+                    z3 = fmaf(h.x, S.w3[16 * cg + 2 * e], fmaf(h.y, S.w3[16 * cg + 2 * e + 1], z3));
+                }
+            }
+            if (j < Hc && i < Wc) out[(int64_t)q * plane + (int64_t)j * Wc + i] = to_out<OutT>(sigmoid(z3));
+            tc_fence_before();  // this iteration's TMEM reads are ordered before the next MMA
+        }
+        __syncthreads();  // every thread is done with this block's cumulants, and the flag is settled
+        if (*abort_flag) break;  // uniform: read after the barrier
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+constexpr size_t kTcSmemBytes = sizeof(TcSmem) + 1024;
 
 // ---- 6. backward: gradient of the mean squared error ---------------------------
 // Per iteration a CTA takes 64 rows (16 per warp).  Each warp runs the forward
@@ -792,13 +1045,44 @@ extern "C" lcp_status lcp_mlp_infer(const float* mom, int H, int W, double dx, d
     if (!mom || !aligned16(mom) || !params || !lcp_out)
         return fail(LCP_ERR_ARG, "lcp_mlp_infer: NULL or misaligned pointer");
     if (out_dtype != LCP_F32 && out_dtype != LCP_F16) return fail(LCP_ERR_ARG, "lcp_mlp_infer: out dtype must be F32 or F16");
-    const dim3 grid((W - 1 + kIC - 1) / kIC, (H - 1 + kIR - 1) / kIR);
-    if (grid.y > 65535) return fail(LCP_ERR_UNSUPPORTED, "lcp_mlp_infer: H too large");
+    const int64_t nblocks = (int64_t)((W - 1 + kIC - 1) / kIC) * ((H - 1 + kIR - 1) / kIR);
+    if (nblocks > INT_MAX) return fail(LCP_ERR_UNSUPPORTED, "lcp_mlp_infer: grid too large");
     const float4* m4 = reinterpret_cast<const float4*>(mom);
     const Spacing sp = make_spacing(dx, dy);
+    {
+        static std::mutex mu;
+        static bool set[64] = {false};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+            cudaGetLastError();
+            return fail(LCP_ERR_CUDA, "lcp_mlp_infer: no usable current device");
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        if (!set[dev]) {
+            // the full shared-memory carveout, so that the occupancy below counts every resident CTA
+            if (cudaFuncSetAttribute(mlp_infer_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kTcSmemBytes) != cudaSuccess ||
+                cudaFuncSetAttribute(mlp_infer_tc_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kTcSmemBytes) != cudaSuccess ||
+                cudaFuncSetAttribute(mlp_infer_tc_kernel<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+                cudaFuncSetAttribute(mlp_infer_tc_kernel<__half>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(LCP_ERR_CUDA, "lcp_mlp_infer: %zu bytes of shared memory not available", kTcSmemBytes);
+            }
+            set[dev] = true;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // persistent: kTcCtasPerSm CTAs per SM (the kernel's launch bounds; its
+    // registers, shared memory and 64 TMEM columns each allow that many), each
+    // walking cell blocks; CTAs beyond what fits wait for a slot (no CTA waits
+    // on another)
+    const int grid = (int)std::min<int64_t>(nblocks, (int64_t)kTcCtasPerSm * num_sms());
     if (out_dtype == LCP_F16)
-        mlp_infer_kernel<__half><<<grid, kMT, 0, (cudaStream_t)stream>>>(m4, H, W, sp, ip, params, (__half*)lcp_out);
+        mlp_infer_tc_kernel<__half><<<grid, kMT, kTcSmemBytes, st>>>(m4, H, W, sp, ip, params, (__half*)lcp_out);
     else
-        mlp_infer_kernel<float><<<grid, kMT, 0, (cudaStream_t)stream>>>(m4, H, W, sp, ip, params, (float*)lcp_out);
+        mlp_infer_tc_kernel<float><<<grid, kMT, kTcSmemBytes, st>>>(m4, H, W, sp, ip, params, (float*)lcp_out);
     return check_launch("lcp_mlp_infer");
 }
