@@ -340,7 +340,7 @@ def our_arm(args):
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": profiled_traffic(), "peak_kind": peak_kind,
-            "kernel": "lcp_fused_ws step: stats_ws_kernel<float,4> + lcp_rows_kernel<8,mask,float>", "alg_bytes_per_launch": alg_bytes,
+            "kernel": "lcp_fused_ws step: stats_ws_kernel<float,4> + lcp_warp_rows_kernel<8,mask,float>", "alg_bytes_per_launch": alg_bytes,
             "kernel_ms": round(kern_ms, 5)}
 
     # end to end through the host-buffer API: pinned members in, LCP + mask out
