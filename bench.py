@@ -661,6 +661,19 @@ def learned_arm(args):
         closed, _ = lib.lcp_fused(u, v, iso, 1.0, 1.0, 0)
         rms_c, max_c = err(closed)
         rms_l, max_l = err(out)
+        # the whole field, judged on the GPU by the exact empirical LCP (interior cells)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        exact_full, _ = lib.lcp_exact_empirical(u, v, iso)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        exact_ms = e0.elapsed_time(e1)
+
+        def err_full(m):
+            e = (m.float() - exact_full)[:, 1:-1, 1:-1]
+            return float(torch.sqrt((e * e).mean())), float(e.abs().max())
+
+        full = {"closed_form_ddof0": err_full(closed), "learned": err_full(out)}
         mc = []
         for S in (100, 1000, 10000):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -669,6 +682,7 @@ def learned_arm(args):
             e1.record(stream)
             torch.cuda.synchronize()
             r, mx = err(est)
+            full[f"mc_S{S}"] = err_full(est)
             mc.append((S, e0.elapsed_time(e1), r, mx))
         c_rms = float(np.median([r * np.sqrt(S) for S, _, r, _ in mc]))
         c_max = float(np.median([mx * np.sqrt(S) for S, _, _, mx in mc]))
@@ -681,7 +695,9 @@ def learned_arm(args):
                "mc_S_at_learned_rms": round(s_rms), "mc_S_at_learned_max": round(s_max),
                "t_mc_over_t_learned_at_equal_rms": round(s_rms * rate / ms_per_step, 1),
                "t_mc_over_t_learned_at_equal_max": round(s_max * rate / ms_per_step, 1),
-               "train_s": round(t_train, 2), "train_final_loss": round(losses[-1], 6)}
+               "train_s": round(t_train, 2), "train_final_loss": round(losses[-1], 6),
+               "full_field_gpu_judge": {"exact_ms": round(exact_ms, 3),
+                                        **{k: {"rms": round(a, 5), "max": round(b, 5)} for k, (a, b) in full.items()}}}
     cpu = learned_cpu_baseline(d) if (not args.no_cpu and rank == 0 and world == 1) else None
 
     e2e = None

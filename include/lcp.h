@@ -361,6 +361,28 @@ lcp_status lcp_mlp_infer(const float* mom, int H, int W, double dx, double dy, c
                          const float* params, void* lcp_out, lcp_dtype out_dtype, lcp_stream_t stream);
 
 /*
+ * lcp_exact_empirical - the exact LCP under the empirical model (every vertex
+ * component an independent uniform draw from its own members): the value the
+ * Monte Carlo estimator of Sec. 3.2 converges to, computed by counting.  At an
+ * interior vertex the Eq. 1 divergence is X + Y with X over the M^2 pairs of
+ * u members at i+1, i-1 and Y over the M^2 pairs of v members at j+1, j-1, so
+ * P(D < c) = #{x + y < c} / M^4 (both lists sorted, counted with two
+ * pointers).  Interior vertex stencils share no value, so for cells whose four
+ * vertices are interior LCP = 1 - prod p - prod (1 - p) exactly.
+ *   u, v       device members [M][H][W] (LCP_F32 or LCP_BF16), M <= 64, H, W >= 4
+ *   iso        HOST, 1 <= K <= 64
+ *   below      device fp32 [K][H][W] scratch: P(D < c) of the interior vertices
+ *   lcp_out    device fp32 [K][H-1][W-1]: the LCP of cells (i, j) with
+ *              1 <= i <= W-3 and 1 <= j <= H-3; NaN elsewhere (the one-sided
+ *              stencils of the outer ring share members)
+ * Arithmetic in FP32 (a pair within rounding of c may count on either side);
+ * counts are exact integers.  Not for NaN members.
+ */
+lcp_status lcp_exact_empirical(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
+                               int64_t member_stride, double dx, double dy, const float* iso, int K, float* below,
+                               float* lcp_out, lcp_stream_t stream);
+
+/*
  * lcp_mc - classical Monte Carlo estimate of the LCP map (Sec. 3.2 and Sec. 4):
  * every sample is one realisation of the whole field; its divergence (Eq. 1,
  * same boundary rule) is tested per cell and isovalue, "crossing" meaning

@@ -38,6 +38,7 @@ __all__ = [
     "Batch",
     "lcp_mc",
     "lcp_philox_fill",
+    "lcp_exact_empirical",
     "lcp_device_status",
     "mask_words_per_row",
     "unpack_mask",
@@ -104,6 +105,8 @@ _SIGNATURES = {
                                   ctypes.c_size_t, c_vp, ctypes.POINTER(lcp_batch_plan)]),
     "lcp_batch": (c_int, [ctypes.POINTER(lcp_batch_plan), ctypes.POINTER(lcp_tune), c_vp]),
     "lcp_batch_autotune": (c_int, [ctypes.POINTER(lcp_batch_plan), c_int, ctypes.POINTER(lcp_tune), c_fp, c_vp]),
+    "lcp_exact_empirical": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_double, c_double, c_fp, c_int,
+                                    c_vp, c_vp, c_vp]),
     "lcp_fused_static_ws": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double, c_fp,
                                     c_int, c_vp, c_int, c_vp, c_vp]),
 }
@@ -370,6 +373,20 @@ def lcp_mc(isovalues, n_samples: int, seed: int, dx: float = 1.0, dy: float = 1.
     _check(lib.lcp_mc(*args, h, w, float(dx), float(dy), iso_p, k, int(n_samples), int(seed) & (2**64 - 1),
                       int(offset) & (2**64 - 1), _ptr(counts), _ptr(est), _stream()))
     return est, counts
+
+
+def lcp_exact_empirical(u, v, isovalues, dx: float = 1.0, dy: float = 1.0, out=None, below=None):
+    """Exact LCP under the empirical model (cells with four interior vertices;
+    NaN elsewhere): fp32 [K, H-1, W-1]; also returns P(D < c) [K, H, W]."""
+    m, h, w, stride = _members(u, v)
+    iso, k, iso_p = _iso(isovalues)
+    if out is None:
+        out = torch.empty((k, h - 1, w - 1), dtype=torch.float32, device=u.device)
+    if below is None:
+        below = torch.empty((k, h, w), dtype=torch.float32, device=u.device)
+    _check(load().lcp_exact_empirical(_ptr(u), _ptr(v), _dtype_code(u.dtype), m, h, w, stride, float(dx), float(dy),
+                                      iso_p, k, _ptr(below), _ptr(out), _stream()))
+    return out, below
 
 
 def lcp_philox_fill(seed: int, c1: int, offset: int, count: int, device="cuda"):
