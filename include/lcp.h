@@ -424,6 +424,72 @@ lcp_status lcp_mc(lcp_mc_mode mode, const float* mu_u, const float* var_u, const
 lcp_status lcp_device_status(uint32_t* flags, int reset);
 
 /*
+ * lcp_speed_gradient - the preprocessing of the Red Sea study (Sec. 4.2,
+ * Fig. 3): per member the velocity magnitude s = sqrt(u^2 + v^2) and its
+ * gradient with the stencil of Eq. 1 and the boundary rule above:
+ *   gx = (s[i+] - s[i-]) / ((i+ - i-) dx),  gy = (s[j+] - s[j-]) / ((j+ - j-) dy).
+ * u, v    device members [M][H][W] (LCP_F32 or LCP_BF16), member_stride as above
+ * gx, gy  device fp32 outputs [M][H][W], contiguous (member stride H*W)
+ * FP32 arithmetic.  Errors: as lcp_stats (ddof is not used), NULL outputs, or
+ * dx, dy <= 0.
+ */
+lcp_status lcp_speed_gradient(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
+                              int64_t member_stride, double dx, double dy, float* gx, float* gy,
+                              lcp_stream_t stream);
+
+/*
+ * lcp_speed_gradient_ws - the closed-form LCP map of the divergence of the
+ * speed gradient (Sec. 4.2, Fig. 3d) with the preprocessing fused into the
+ * statistics pass: every member value is read once, no gradient member is
+ * stored, and the result equals lcp_fused_ws on the members of
+ * lcp_speed_gradient up to FP32 rounding.  Arguments as lcp_fused_ws (the
+ * workspace is sized by lcp_fused_workspace_bytes and must be non-NULL);
+ * H * W < 2^31.
+ */
+lcp_status lcp_speed_gradient_ws(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
+                                 int64_t member_stride, int ddof, double dx, double dy, const float* iso, int K,
+                                 void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, void* workspace,
+                                 size_t workspace_bytes, lcp_stream_t stream);
+
+/*
+ * lcp_colormap - colour mapping of a scalar map into a headless RGBA8 buffer.
+ * Sec. 3.1 (last paragraph) shows the LCP map by colour mapping, and Sec. 4.2
+ * clamps the mean-field divergence to a display range before mapping it
+ * (Fig. 3c).  No graphics API is involved: the result is plain bytes in device
+ * memory.
+ *
+ * values  device fp32 [planes][rows][cols] (contiguous), e.g. an LCP map
+ *         [K][H-1][W-1]
+ * vmin, vmax   display range, finite, vmin < vmax
+ * stops   HOST array of n_stops x 5 floats (t, r, g, b, a), every entry in
+ *         [0, 1], t strictly increasing from exactly 0 to exactly 1;
+ *         2 <= n_stops <= LCP_MAX_COLOR_STOPS
+ * nan_rgba   packed colour (r | g << 8 | b << 16 | a << 24) of NaN values
+ * mask    optional device crossing bits for rows x cols cells in the library's
+ *         mask layout ([planes][rows][ceil(cols/32)] uint32), or NULL; a set
+ *         bit paints mask_rgba (the mean-field contour cells, Fig. 1a)
+ * rgba    device uint8 [planes][rows][cols][4], bytes r, g, b, a per value
+ *
+ * Per value x, with every operation a single IEEE fp32 operation rounded to
+ * nearest (no fused multiply-add), so that any fp32 implementation of these
+ * steps produces the same bytes:
+ *   x NaN -> nan_rgba; else if the mask bit is set -> mask_rgba; else
+ *   t  = min(max((x - vmin) / (vmax - vmin), 0), 1)
+ *   s  = the largest stop index <= n_stops - 2 with t_s <= t
+ *   f  = (t - t_s) / (t_{s+1} - t_s)
+ *   ch = c_s + f * (c_{s+1} - c_s)                  for each of r, g, b, a
+ *   byte = min(max(floor(ch * 255 + 0.5), 0), 255)
+ * Alignment: values, mask and rgba 4-byte aligned (16 bytes gives vector
+ * access).  Errors: LCP_ERR_ARG for a negative size, NULL pointers (n > 0),
+ * a bad range or stop table, or misalignment.  planes * rows * cols == 0 is a
+ * no-op.
+ */
+#define LCP_MAX_COLOR_STOPS 16
+lcp_status lcp_colormap(const float* values, int planes, int rows, int cols, float vmin, float vmax,
+                        const float* stops, int n_stops, uint32_t nan_rgba, const uint32_t* mask,
+                        uint32_t mask_rgba, uint8_t* rgba, lcp_stream_t stream);
+
+/*
  * lcp_philox_fill - the Monte Carlo generator's raw words, for testing and
  * for reproducible inputs: out[4 n + r] = word r of Philox-4x32-10 with counter
  * (n, c1, offset lo, offset hi) and key (seed lo, seed hi), n in [0, count).

@@ -23,8 +23,12 @@ divergence cumulants, features, the network and Adam of the learned surrogate)
 is pinned by ``tests/test_oracle_surrogate.py``: exact rational moments, the
 divergence's exact distribution enumerated over every stencil combination,
 hand-evaluated networks, a finite-difference gradient check and Adam's
-first-step property.
+first-step property.  ``viz`` (the colour map and the isocontour segments)
+is pinned by ``tests/test_oracle_viz.py``: exact integer byte formulas on dyadic
+inputs, the stops' own colours, special values, and marching squares against
+hand-drawn cases and the crossing mask.
 """
 
 from .lcp_oracle import *  # noqa: F401,F403
 from . import surrogate  # noqa: F401,E402
+from . import viz  # noqa: F401,E402

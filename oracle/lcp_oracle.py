@@ -34,6 +34,11 @@ R9  The Monte Carlo baseline (Sec. 3.2, Sec. 4) samples the fitted per-vertex
     Gaussians; each sample is one realisation of the whole field.
 R12 Empirical (non-Gaussian) model: every vertex component is an independent
     draw from its own ensemble members, uniformly.
+R19 Speed-gradient preprocessing (Sec. 4.2, Red Sea): per member the velocity
+    magnitude s = sqrt(u^2 + v^2) and its "pixelwise gradient" with the stencil
+    of Eq. 1 (central differences inside, first-order one-sided at the ends,
+    spacing dx, dy); the gradient vectors are then the ensemble whose
+    divergence LCP is mapped, every step of the closed form unchanged.
 """
 
 from __future__ import annotations
@@ -59,6 +64,8 @@ __all__ = [
     "exact_empirical_below",
     "exact_empirical_lcp",
     "sum_squared_error",
+    "speed_gradient",
+    "speed_gradient_lcp",
 ]
 
 
@@ -419,3 +426,33 @@ def sum_squared_error(a, b):
     """SSE between two LCP maps (Sec. 4, accuracy of MC against the analytical LCP)."""
     d = np.asarray(a, np.float64) - np.asarray(b, np.float64)
     return float((d * d).sum())
+
+
+# --------------------------------------------------------------------------
+# Sec. 4.2 (Red Sea): divergence of the gradient of the velocity magnitude
+# --------------------------------------------------------------------------
+def speed_gradient(u, v, dx: float, dy: float):
+    """Per member, the gradient of the velocity magnitude (reading R19).
+
+    s = sqrt(u^2 + v^2);  gx = (s[i+] - s[i-]) / ((i+ - i-) dx),
+    gy = (s[j+] - s[j-]) / ((j+ - j-) dy), with the neighbours of
+    ``stencil_neighbours`` (central inside, one-sided at the ends).
+
+    u, v : [..., H, W];  returns (gx, gy) float64 of the same shape
+    """
+    u = np.asarray(u, np.float64)
+    v = np.asarray(v, np.float64)
+    s = np.sqrt(u * u + v * v)
+    h, w = s.shape[-2:]
+    ilo, ihi, isteps = stencil_neighbours(w)
+    jlo, jhi, jsteps = stencil_neighbours(h)
+    gx = (s[..., :, ihi] - s[..., :, ilo]) / (isteps * float(dx))
+    gy = (s[..., jhi, :] - s[..., jlo, :]) / (jsteps * float(dy))[:, None]
+    return gx, gy
+
+
+def speed_gradient_lcp(u, v, dx: float, dy: float, isovalues, ddof: int = 1):
+    """The closed-form path on the speed-gradient ensemble (Sec. 4.2, Fig. 3d):
+    ``lcp_closed_form`` of the members' (gx, gy).  returns its dict."""
+    gx, gy = speed_gradient(u, v, dx, dy)
+    return lcp_closed_form(gx, gy, dx, dy, isovalues, ddof)

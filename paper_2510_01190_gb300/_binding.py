@@ -39,6 +39,11 @@ __all__ = [
     "lcp_mc",
     "lcp_philox_fill",
     "lcp_exact_empirical",
+    "lcp_colormap",
+    "lcp_speed_gradient",
+    "lcp_speed_gradient_ws",
+    "DEFAULT_STOPS",
+    "pack_rgba",
     "lcp_device_status",
     "mask_words_per_row",
     "unpack_mask",
@@ -107,6 +112,12 @@ _SIGNATURES = {
     "lcp_batch_autotune": (c_int, [ctypes.POINTER(lcp_batch_plan), c_int, ctypes.POINTER(lcp_tune), c_fp, c_vp]),
     "lcp_exact_empirical": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_double, c_double, c_fp, c_int,
                                     c_vp, c_vp, c_vp]),
+    "lcp_speed_gradient": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_double, c_double, c_vp, c_vp,
+                                   c_vp]),
+    "lcp_speed_gradient_ws": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double,
+                                      c_fp, c_int, c_vp, c_int, c_vp, c_vp, ctypes.c_size_t, c_vp]),
+    "lcp_colormap": (c_int, [c_vp, c_int, c_int, c_int, ctypes.c_float, ctypes.c_float, c_fp, c_int, c_u32, c_vp,
+                             c_u32, c_vp, c_vp]),
     "lcp_fused_static_ws": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double, c_fp,
                                     c_int, c_vp, c_int, c_vp, c_vp]),
 }
@@ -307,6 +318,38 @@ def lcp_fused_static_ws(u, v, isovalues, dx: float = 1.0, dy: float = 1.0, ddof:
     return out, mask_out
 
 
+def lcp_speed_gradient(u, v, dx: float = 1.0, dy: float = 1.0):
+    """Gradient of every member's velocity magnitude (Sec. 4.2 preprocessing):
+    returns (gx, gy), float32 [M, H, W]."""
+    m, h, w, stride = _members(u, v)
+    gx = torch.empty((m, h, w), dtype=torch.float32, device=u.device)
+    gy = torch.empty_like(gx)
+    _check(load().lcp_speed_gradient(_ptr(u), _ptr(v), _dtype_code(u.dtype), m, h, w, stride, float(dx), float(dy),
+                                     _ptr(gx), _ptr(gy), _stream()))
+    return gx, gy
+
+
+def lcp_speed_gradient_ws(u, v, isovalues, dx: float = 1.0, dy: float = 1.0, ddof: int = 1,
+                          out_dtype=torch.float32, mask: bool = False, out=None, mask_out=None, workspace=None):
+    """LCP map of the divergence of the members' speed gradients, the
+    preprocessing fused into the statistics pass (Sec. 4.2, Fig. 3d).
+    Returns (lcp, mask_words|None)."""
+    m, h, w, stride = _members(u, v)
+    iso, k, iso_p = _iso(isovalues)
+    out, mask_out = _outputs(k, h, w, u.device, out_dtype, mask, out, mask_out)
+    lib = load()
+    need = int(lib.lcp_fused_workspace_bytes(m, h, w, _dtype_code(u.dtype)))
+    if workspace is None:
+        _, ws_ptr = _workspace(need, u.device)
+        ws_bytes = need
+    else:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    _check(lib.lcp_speed_gradient_ws(_ptr(u), _ptr(v), _dtype_code(u.dtype), m, h, w, stride, ddof, float(dx),
+                                     float(dy), iso_p, k, _ptr(out), _dtype_code(out.dtype), _ptr(mask_out),
+                                     c_vp(ws_ptr), ws_bytes, _stream()))
+    return out, mask_out
+
+
 class _HostStaging:
     """Device buffers reused by ``lcp_fused_host`` across calls of one shape."""
 
@@ -492,3 +535,49 @@ def unpack_mask(mask_words, w: int):
     shifts = torch.arange(32, device=words.device, dtype=torch.int64)
     bits = (words[..., None] >> shifts) & 1
     return bits.reshape(*words.shape[:-1], -1)[..., : w - 1].to(torch.bool)
+
+
+# ---------------------------------------------------------------------------
+# Colour mapping into a headless RGBA8 buffer
+# ---------------------------------------------------------------------------
+# (t, r, g, b, a): dark blue -> blue -> cyan -> yellow -> red -> dark red, the
+# usual rainbow ramp for divergence and probability maps (sinks blue, sources red)
+DEFAULT_STOPS = [
+    (0.0, 0.0, 0.0, 0.5, 1.0),
+    (0.125, 0.0, 0.0, 1.0, 1.0),
+    (0.375, 0.0, 1.0, 1.0, 1.0),
+    (0.625, 1.0, 1.0, 0.0, 1.0),
+    (0.875, 1.0, 0.0, 0.0, 1.0),
+    (1.0, 0.5, 0.0, 0.0, 1.0),
+]
+
+
+def pack_rgba(r: int, g: int, b: int, a: int = 255) -> int:
+    """Packed colour word r | g << 8 | b << 16 | a << 24 of ``lcp_colormap``."""
+    return (int(r) & 255) | ((int(g) & 255) << 8) | ((int(b) & 255) << 16) | ((int(a) & 255) << 24)
+
+
+def lcp_colormap(values, vmin: float = 0.0, vmax: float = 1.0, stops=None, nan_rgba: int = 0, mask=None,
+                 mask_rgba: int = 0xFF000000, out=None):
+    """RGBA8 image of a scalar map (``[rows, cols]`` or ``[planes, rows, cols]``
+    float32 CUDA tensor, e.g. an LCP map): returns uint8 ``[..., rows, cols, 4]``.
+    ``mask`` is the library's crossing-mask words for those cells (as returned by
+    ``lcp_fused(..., mask=True)``); set bits paint ``mask_rgba``."""
+    if values.dtype != torch.float32 or not values.is_cuda or not values.is_contiguous() or values.dim() not in (2, 3):
+        raise ValueError("values must be a contiguous float32 CUDA tensor [rows, cols] or [planes, rows, cols]")
+    planes, rows, cols = (1, *values.shape) if values.dim() == 2 else tuple(values.shape)
+    st = torch.as_tensor(stops if stops is not None else DEFAULT_STOPS, dtype=torch.float32).reshape(-1).contiguous()
+    if st.numel() % 5:
+        raise ValueError("stops must be rows of (t, r, g, b, a)")
+    if mask is not None:
+        nw = (cols + 31) // 32
+        if mask.dtype != torch.int32 or not mask.is_cuda or not mask.is_contiguous() or mask.numel() != planes * rows * nw:
+            raise ValueError(f"mask must be contiguous int32 CUDA words [{planes}, {rows}, {nw}]")
+    if out is None:
+        out = torch.empty(tuple(values.shape) + (4,), dtype=torch.uint8, device=values.device)
+    elif out.dtype != torch.uint8 or out.numel() != values.numel() * 4 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous uint8 tensor with 4 bytes per value")
+    _check(load().lcp_colormap(_ptr(values), planes, rows, cols, float(vmin), float(vmax),
+                               ctypes.cast(st.data_ptr(), c_fp), st.numel() // 5, int(nan_rgba) & 0xFFFFFFFF,
+                               _ptr(mask), int(mask_rgba) & 0xFFFFFFFF, _ptr(out), _stream()))
+    return out

@@ -101,9 +101,6 @@ __device__ __forceinline__ void st_keep_f4(float* p, float4 v, uint64_t pol) {
                  "f"(v.w), "l"(pol)
                  : "memory");
 }
-__device__ __forceinline__ void st_keep_f1(float* p, float v, uint64_t pol) {
-    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
-}
 
 template <typename T, int VEC>
 struct SLoad;
@@ -130,12 +127,6 @@ struct SLoad<__nv_bfloat16, 4> {
         x[2] = __uint_as_float(r.y << 16);
         x[3] = __uint_as_float(r.y & 0xFFFF0000u);
     }
-};
-template <>
-struct SLoad<__nv_bfloat16, 8> {
-    using raw_t = uint4;
-    static __device__ __forceinline__ raw_t load(const __nv_bfloat16* p, uint64_t pol) { return ld_stream_u4(p, pol); }
-    static __device__ __forceinline__ void cvt(const raw_t& r, float* x) { Loader<__nv_bfloat16, 8>::cvt(r, x); }
 };
 template <typename T>
 __device__ __forceinline__ float load1(const T* p) {
@@ -771,7 +762,7 @@ lcp_status launch_rows_chunk(const RowsParams& p, const IsoParams& ip, cudaStrea
 // Isovalues in passes whose sizes are the binary digits of K (largest first,
 // at most 32 each): every pass runs a kernel specialised for its exact count.
 template <typename OutT>
-lcp_status launch_rows(const RowsParams& p0, const float* iso, int K, cudaStream_t st) {
+lcp_status launch_rows(const RowsParams& p0, const float* iso, int K, cudaStream_t st, bool pdl = true) {
     RowsParams p = p0;
     int kb = 0;
     const bool warp_rows = K <= 8;
@@ -783,10 +774,10 @@ lcp_status launch_rows(const RowsParams& p0, const float* iso, int K, cudaStream
         ip.K = chunk;
         for (int k = 0; k < chunk; ++k) ip.c[k] = iso[kb + k];
         p.kbase = kb;
-        // every pass is a programmatic dependent of the kernel before it: each
-        // waits on the counters of its rows, not on stream order
-        const lcp_status s = p.mask ? launch_rows_chunk<true, OutT>(p, ip, st, true, warp_rows)
-                                    : launch_rows_chunk<false, OutT>(p, ip, st, true, warp_rows);
+        // with counters every pass is a programmatic dependent of the kernel
+        // before it and waits on the counters of its rows; without, stream order
+        const lcp_status s = p.mask ? launch_rows_chunk<true, OutT>(p, ip, st, pdl, warp_rows)
+                                    : launch_rows_chunk<false, OutT>(p, ip, st, pdl, warp_rows);
         if (s != LCP_OK) return s;
         kb += chunk;
     }
@@ -854,6 +845,37 @@ lcp_status run(const void* u, const void* v, int M, int H, int W, int64_t stride
 }
 
 }  // namespace
+
+WsGeometry ws_geometry(int H, int W) {
+    const Layout L = layout(H, W);
+    WsGeometry g;
+    g.band_rows = L.band_rows;
+    g.ctr_bytes = L.ctr_bytes;
+    g.plane_bytes = L.plane_bytes;
+    g.total = L.total;
+    return g;
+}
+
+lcp_status ws_lcp_rows(const float4* rec, int64_t ps, int row0, int H, int W, int r0, int r1, double dx, double dy,
+                       const float* iso, int K, void* out, lcp_dtype out_dtype, uint32_t* mask, cudaStream_t st) {
+    RowsParams rp;
+    rp.st = rec;
+    rp.ps = ps;
+    rp.row0 = row0;
+    rp.H = H;
+    rp.W = W;
+    rp.r_begin = r0;
+    rp.r_end = r1;
+    rp.sp = make_spacing(dx, dy);
+    rp.out = out;
+    rp.mask = mask;
+    rp.n_words = (W - 1 + 31) / 32;
+    rp.kbase = 0;
+    rp.dep = nullptr;  // records complete before this launch (stream order)
+    rp.n_begin = 0;
+    rp.sv = 1;
+    return out_dtype == LCP_F16 ? launch_rows<__half>(rp, iso, K, st, false) : launch_rows<float>(rp, iso, K, st, false);
+}
 
 uint32_t read_ws_status(bool reset) {
     uint32_t f = 0;

@@ -299,6 +299,21 @@ lcp_status fused_tma(const void* u, const void* v, lcp_dtype in_dtype, int M, in
 uint32_t read_tma_status(bool reset);  // TMA row-march pipeline (mbarrier waits)
 uint32_t read_ws_status(bool reset);   // workspace path (LCP blocks waiting on statistics rows)
 
+// Workspace of lcp_fused_ws: bands of `band_rows` cell rows; a counter header of
+// ctr_bytes, then two record planes (u, v) of plane_bytes each.  A record is
+// float4 (x0, delta, var, 0) per vertex and component: member 0, the FP32 mean
+// of the members shifted by member 0, and the variance.
+struct WsGeometry {
+    int band_rows;
+    size_t ctr_bytes, plane_bytes, total;
+};
+WsGeometry ws_geometry(int H, int W);
+// Eqs. 2/3 and the LCP of cell rows [r0, r1) (plus the mask) from such record
+// planes, whose row 0 is grid row row0 and which hold rows max(r0-1, 0) ..
+// min(r1+1, H-1); launched in stream order after the kernel that wrote them.
+lcp_status ws_lcp_rows(const float4* rec, int64_t ps, int row0, int H, int W, int r0, int r1, double dx, double dy,
+                       const float* iso, int K, void* out, lcp_dtype out_dtype, uint32_t* mask, cudaStream_t st);
+
 inline lcp_status check_spacing(const char* fn, double dx, double dy) {
     if (!(dx > 0.0) || !(dy > 0.0) || dx > 1e30 || dy > 1e30)
         return fail(LCP_ERR_ARG, "%s: dx and dy must be finite and > 0", fn);

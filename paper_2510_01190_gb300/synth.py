@@ -210,6 +210,13 @@ def eddy_ensemble_torch(seed: int = 0, h: int = 8192, w: int = 8192, m: int = 20
     return dict(u=u, v=v, dx=1.0, dy=1.0, isovalues=iso)
 
 
+# Isovalues for the divergence of the speed gradient of an eddy ensemble
+# (Sec. 4.2 maps sources at 0.003 on the Red Sea).  With noise 0.05 per member
+# the mean-field value is noise-dominated at about 0.01, so the table brackets
+# it: a sink level, zero, the paper's source level, a source level.
+EDDY_GRADIENT_ISOVALUES = np.array([-0.01, 0.0, 0.003, 0.01], np.float32)
+
+
 # ---------------------------------------------------------------------------
 # 1024^2 non-Gaussian: skew-normal or 2-component Gaussian-mixture noise
 # ---------------------------------------------------------------------------

@@ -100,3 +100,37 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_binding, "library_path", lambda: str(tmp_path / "absent.so"))
     with pytest.raises(_binding.LcpError):
         _binding.load(build_if_stale=False)
+
+
+def test_colormap_rejects_bad_arguments(clib):
+    f = clib.lcp_colormap
+    good = (ctypes.c_float * 10)(0.0, 0, 0, 0, 1, 1.0, 1, 1, 1, 1)
+    assert f(FAKE, 1, 4, 4, 1.0, 1.0, good, 2, 0, None, 0, FAKE, None) == -1 and "vmin < vmax" in _err(clib)
+    assert f(FAKE, 1, 4, 4, 0.0, float("nan"), good, 2, 0, None, 0, FAKE, None) == -1
+    assert f(FAKE, 1, 4, 4, 0.0, 1.0, good, 1, 0, None, 0, FAKE, None) == -1 and "stops" in _err(clib)
+    assert f(FAKE, 1, 4, 4, 0.0, 1.0, None, 2, 0, None, 0, FAKE, None) == -1
+    back = (ctypes.c_float * 10)(1.0, 0, 0, 0, 1, 0.0, 1, 1, 1, 1)
+    assert f(FAKE, 1, 4, 4, 0.0, 1.0, back, 2, 0, None, 0, FAKE, None) == -1 and "increase" in _err(clib)
+    short = (ctypes.c_float * 10)(0.0, 0, 0, 0, 1, 0.5, 1, 1, 1, 1)
+    assert f(FAKE, 1, 4, 4, 0.0, 1.0, short, 2, 0, None, 0, FAKE, None) == -1 and "last at 1" in _err(clib)
+    bright = (ctypes.c_float * 10)(0.0, 0, 0, 0, 1, 1.0, 2, 1, 1, 1)
+    assert f(FAKE, 1, 4, 4, 0.0, 1.0, bright, 2, 0, None, 0, FAKE, None) == -1 and "outside" in _err(clib)
+    assert f(FAKE, -1, 4, 4, 0.0, 1.0, good, 2, 0, None, 0, FAKE, None) == -1
+    assert f(None, 1, 4, 4, 0.0, 1.0, good, 2, 0, None, 0, FAKE, None) == -1 and "NULL" in _err(clib)
+    assert f(ctypes.c_void_p(258), 1, 4, 4, 0.0, 1.0, good, 2, 0, None, 0, FAKE, None) == -1
+    assert f(None, 0, 4, 4, 0.0, 1.0, good, 2, 0, None, 0, None, None) == 0  # empty: nothing to do
+
+
+def test_speed_gradient_rejects_bad_arguments(clib):
+    iso = (ctypes.c_float * 2)(0.0, 1.0)
+    g = clib.lcp_speed_gradient
+    assert g(FAKE, FAKE, 0, 4, 8, 8, 64, 1.0, 1.0, FAKE, None, None) == -1 and "NULL" in _err(clib)
+    assert g(FAKE, FAKE, 0, 4, 8, 8, 64, 0.0, 1.0, FAKE, FAKE, None) == -1 and "dx and dy" in _err(clib)
+    assert g(FAKE, FAKE, 0, 4, 8, 8, 63, 1.0, 1.0, FAKE, FAKE, None) == -1 and "member_stride" in _err(clib)
+    f = clib.lcp_speed_gradient_ws
+    args = [FAKE, FAKE, 0, 4, 8, 8, 64, 1, 1.0, 1.0, iso, 2, FAKE, 0, None]
+    assert f(*args, None, 0, None) == -1 and "workspace" in _err(clib)
+    assert f(*args, ctypes.c_void_p(512), 16, None) == -1 and "too small" in _err(clib)
+    assert f(*args, ctypes.c_void_p(520), 1 << 30, None) == -1 and "aligned" in _err(clib)
+    big = [FAKE, FAKE, 0, 2, 65536, 32768, 65536 * 32768, 1, 1.0, 1.0, iso, 2, FAKE, 0, None]
+    assert f(*big, ctypes.c_void_p(512), 1 << 40, None) == -3 and "2^31" in _err(clib)
