@@ -49,13 +49,17 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-mc", action="store_true", help="skip the Monte Carlo equal-error comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--workload", choices=["latlon", "batch", "learned", "ocean"], default="latlon",
-                    help="latlon: the 721x1440 field (default); batch: 256 uneven fields in one persistent launch")
+    ap.add_argument("--workload", choices=["latlon", "batch", "learned", "ocean", "redsea", "colormap"],
+                    default="latlon",
+                    help="latlon: the 721x1440 field (default); batch: 256 uneven fields in one persistent launch; "
+                         "learned: the non-Gaussian surrogate; ocean: 8192^2 bf16; redsea: the speed-gradient "
+                         "preprocessing of the 8192^2 eddy field; colormap: RGBA8 of its LCP map")
     ap.add_argument("--tile", type=str, default=None,
                     help="batch workload: force the tile shape ROWS,COLS instead of autotuning")
     ap.add_argument("--train-epochs", type=int, default=20, help="learned workload: training epochs (untimed)")
     ap.add_argument("--rows", type=int, default=8192,
-                    help="ocean workload: grid rows (the 8192 x 8192 field by default; fewer rows make small profiling cases)")
+                    help="ocean / redsea / colormap workloads: grid rows (8192 by default; fewer rows make small "
+                         "profiling cases)")
     ap.add_argument("--fields", type=int, default=256,
                     help="batch workload: use the first N of its 256 field descriptors (small cases for profiling)")
     return ap.parse_args()
@@ -852,6 +856,219 @@ def ocean_arm(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Shared plumbing of the NEXT-row workloads (one field per rank, weak scaling)
+# ---------------------------------------------------------------------------
+def gpu_setup():
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = False
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = True
+    import paper_2510_01190_gb300 as lib
+
+    lib.load()
+    return torch, lib, dev, world, rank, local, pg
+
+
+def timed_steps(torch, step, n, warmup, local, pg, dev):
+    """W warm-up steps, then n steps each bracketed by CUDA events on the
+    current stream, with clocks sampled during the timed region.  Returns
+    (max-over-ranks total ms, mean per-step event ms, clocks summary)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(max(warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local).start()
+    time.sleep(0.35)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    if pg:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for i in range(n):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if pg:
+        torch.distributed.barrier()
+    time.sleep(0.25)
+    clocks.stop()
+    total_ms = max_over_ranks(ev[0][0].elapsed_time(ev[-1][1]), device=dev)
+    kern_ms = sum(a.elapsed_time(b) for a, b in ev) / n
+    return total_ms, kern_ms, clocks.summary(t0, t1)
+
+
+def _finish(torch, pg, line, rank):
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+REDSEA_WORKLOAD = ("redsea 8192x8192, 20 members bf16 (5000 Gaussian eddies + noise 0.05), divergence of the "
+                   "speed gradient (Sec. 4.2 preprocessing fused into the statistics pass), 4 isovalues, fp32 maps")
+
+
+def redsea_arm(args):
+    """Speed-gradient preprocessing (Sec. 4.2) on the 8192^2 eddy field."""
+    torch, lib, dev, world, rank, local, pg = gpu_setup()
+    from paper_2510_01190_gb300 import synth
+
+    d = synth.eddy_ensemble_torch(rank, h=max(3, args.rows), device=dev)
+    u, v = d["u"], d["v"]
+    iso = synth.EDDY_GRADIENT_ISOVALUES
+    Mm, Hh, Ww = u.shape
+    Kk, Hc, Wc = len(iso), Hh - 1, Ww - 1
+    out = torch.empty((Kk, Hc, Wc), dtype=torch.float32, device=dev)
+
+    def step():
+        lib.lcp_speed_gradient_ws(u, v, iso, 1.0, 1.0, 1, out=out)
+
+    total_ms, kern_ms, clocks = timed_steps(torch, step, args.steps, args.warmup, local, pg, dev)
+    n = args.steps
+    ms_per_step = total_ms / n
+    value = weak_scaling_value(Hc * Wc, world, ms_per_step)
+    alg = 2 * Mm * Hh * Ww * 2 + Kk * Hc * Wc * 4
+    peak, peak_kind = measured_hbm_peak()
+    achieved = alg / (kern_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": profiled_traffic("lcp_speed_gradient_8192_m20_bf16_k4.md",
+                                        ("gradient.cu", "fused_ws.cu", "lcp_common.cuh")),
+            "peak_kind": peak_kind,
+            "kernel": "lcp_speed_gradient_ws step: grad_stats_kernel<bf16> + lcp_warp_rows_kernel<4,nomask,float> "
+                      "per row band", "alg_bytes_per_launch": alg, "kernel_ms": round(kern_ms, 4)}
+    # the same map in two steps: gradient members materialised in HBM, then lcp_fused_ws
+    unfused = None
+    if rank == 0 and Hh * Ww * Mm * 16 < 0.5 * torch.cuda.get_device_properties(dev).total_memory:
+        two = torch.empty_like(out)
+
+        def step2():
+            g = lib.lcp_speed_gradient(u, v)
+            lib.lcp_fused_ws(g[0], g[1], iso, out=two)
+
+        for _ in range(3):
+            step2()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n2 = max(3, min(20, n))
+        e0.record()
+        for _ in range(n2):
+            step2()
+        e1.record()
+        torch.cuda.synchronize()
+        unfused = {"ms_per_step": round(e0.elapsed_time(e1) / n2, 4),
+                   "what": "lcp_speed_gradient (fp32 gradient members to HBM) then lcp_fused_ws on them",
+                   "max_abs_diff_vs_fused": float(torch.max(torch.abs(two - out)).item())}
+        del two
+        torch.cuda.empty_cache()
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        import oracle as O
+
+        rows, cols, cells, nb, t0 = 33, 2048, 0, 0, time.perf_counter()
+        while time.perf_counter() - t0 < 12.0:
+            j0 = (nb * 977) % (Hh - rows)
+            O.speed_gradient_lcp(u[:, j0:j0 + rows, :cols].float().cpu().numpy(),
+                                 v[:, j0:j0 + rows, :cols].float().cpu().numpy(), 1.0, 1.0, iso)
+            cells += (rows - 1) * (cols - 1)
+            nb += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nb} bands of {rows} rows x {cols} cols x {Mm} members, K={Kk} (FP64 numpy, one thread)",
+               "seconds": round(dt, 2)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 members, f32 arithmetic", "data": "synthetic",
+        "config": {"workload": REDSEA_WORKLOAD if Hh == 8192 else f"{Hh} rows of: " + REDSEA_WORKLOAD, "H": Hh,
+                   "W": Ww, "M": Mm, "K": Kk, "isovalues": [float(c) for c in iso], "global_batch": world,
+                   "parallelism": f"independent fields x{world}" if world > 1 else "single",
+                   "l2": f"no flush: inputs {2 * Mm * Hh * Ww * 2 / 1e9:.1f} GB > 129 MB L2",
+                   "lcp_values_per_s": value * Kk, "hbm_frac_of_measured": roof["frac"]},
+        "roofline": roof, "unfused": unfused, "cpu_baseline": cpu, "e2e": None,
+        "e2e_note": "not measured for this line: 5.4 GB of members per step would be pinned on the host",
+        "clocks": clocks, "gpu_launches": 2 * ws_row_bands(Hh, Ww) * n, "gpu": torch.cuda.get_device_name(dev),
+    }
+    return _finish(torch, pg, line, rank)
+
+
+COLORMAP_WORKLOAD = ("colormap of the 8192x8192 eddy field's LCP map (4 isovalues, fp32 [4][8191][8191]) with its "
+                     "mean-field contour mask, default 6-stop ramp, to RGBA8")
+
+
+def colormap_arm(args):
+    """RGBA8 image of an LCP map (Sec. 3.1, last paragraph) with the mean-field
+    contour cells painted (Fig. 1a): a 4-byte-in, 4-byte-out stream."""
+    torch, lib, dev, world, rank, local, pg = gpu_setup()
+    from paper_2510_01190_gb300 import synth
+
+    d = synth.eddy_ensemble_torch(rank, h=max(3, args.rows), device=dev)
+    lcp, mask = lib.lcp_fused_ws(d["u"], d["v"], d["isovalues"], mask=True)
+    del d
+    torch.cuda.empty_cache()
+    Kk, Hc, Wc = lcp.shape
+    rgba = torch.empty((Kk, Hc, Wc, 4), dtype=torch.uint8, device=dev)
+
+    def step():
+        lib.lcp_colormap(lcp, 0.0, 1.0, mask=mask, out=rgba)
+
+    total_ms, kern_ms, clocks = timed_steps(torch, step, args.steps, args.warmup, local, pg, dev)
+    n = args.steps
+    ms_per_step = total_ms / n
+    values = Kk * Hc * Wc
+    value = weak_scaling_value(Hc * Wc, world, ms_per_step)
+    alg = values * 8 + mask.numel() * 4
+    peak, peak_kind = measured_hbm_peak()
+    achieved = alg / (kern_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": profiled_traffic("lcp_colormap_4x8191x8191.md", ("colormap.cu", "lcp_common.cuh")),
+            "peak_kind": peak_kind, "kernel": "colormap_kernel<mask,uint32>", "alg_bytes_per_launch": alg,
+            "kernel_ms": round(kern_ms, 4)}
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        from oracle import viz as V
+
+        stops = lib.DEFAULT_STOPS
+        rows, done, nb, t0 = 256, 0, 0, time.perf_counter()
+        while time.perf_counter() - t0 < 10.0:
+            k, j0 = nb % Kk, (nb * 977) % (Hc - rows)
+            x = lcp[k, j0:j0 + rows].cpu().numpy()
+            bits = lib.unpack_mask(mask[k:k + 1, j0:j0 + rows], Wc + 1)[0].cpu().numpy()
+            V.colormap_rgba(x, 0.0, 1.0, stops, mask=bits, mask_rgba=0xFF000000)
+            done += rows * Wc
+            nb += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": done / Kk / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nb} bands of {rows} rows x {Wc} values (fp32 numpy, one thread)",
+               "seconds": round(dt, 2)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 in, u8 RGBA out", "data": "synthetic",
+        "config": {"workload": COLORMAP_WORKLOAD if Hc == 8191 else f"{Hc + 1} rows of: " + COLORMAP_WORKLOAD,
+                   "planes": Kk, "rows": Hc, "cols": Wc, "global_batch": world,
+                   "parallelism": f"independent maps x{world}" if world > 1 else "single",
+                   "l2": f"no flush: input {values * 4 / 1e9:.2f} GB > 129 MB L2", "values_per_s": value * Kk,
+                   "hbm_frac_of_measured": roof["frac"]},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": None,
+        "e2e_note": "not measured for this line: the map is produced on the device by the LCP path",
+        "clocks": clocks, "gpu_launches": n, "gpu": torch.cuda.get_device_name(dev),
+    }
+    return _finish(torch, pg, line, rank)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -862,6 +1079,10 @@ def main():
         return learned_arm(args)
     if args.workload == "ocean":
         return ocean_arm(args)
+    if args.workload == "redsea":
+        return redsea_arm(args)
+    if args.workload == "colormap":
+        return colormap_arm(args)
     return our_arm(args)
 
 

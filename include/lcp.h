@@ -470,15 +470,19 @@ lcp_status lcp_speed_gradient_ws(const void* u, const void* v, lcp_dtype in_dtyp
  *         bit paints mask_rgba (the mean-field contour cells, Fig. 1a)
  * rgba    device uint8 [planes][rows][cols][4], bytes r, g, b, a per value
  *
- * Per value x, with every operation a single IEEE fp32 operation rounded to
- * nearest (no fused multiply-add), so that any fp32 implementation of these
- * steps produces the same bytes:
+ * Every operation below is a single IEEE fp32 operation rounded to nearest
+ * (no fused multiply-add), so that any fp32 implementation of these steps
+ * produces the same bytes.  Once per call:
+ *   R = 1 / (vmax - vmin);  per stop segment s < n_stops - 1:
+ *   r_s = 1 / (t_{s+1} - t_s),  d_s = c_{s+1} - c_s   (each of r, g, b, a)
+ * then per value x:
  *   x NaN -> nan_rgba; else if the mask bit is set -> mask_rgba; else
- *   t  = min(max((x - vmin) / (vmax - vmin), 0), 1)
+ *   t  = min(max((x - vmin) * R, 0), 1)
  *   s  = the largest stop index <= n_stops - 2 with t_s <= t
- *   f  = (t - t_s) / (t_{s+1} - t_s)
- *   ch = c_s + f * (c_{s+1} - c_s)                  for each of r, g, b, a
+ *   f  = (t - t_s) * r_s
+ *   ch = c_s + f * d_s                               for each of r, g, b, a
  *   byte = min(max(floor(ch * 255 + 0.5), 0), 255)
+ * where max and min return the non-NaN operand (IEEE maxNum / minNum).
  * Alignment: values, mask and rgba 4-byte aligned (16 bytes gives vector
  * access).  Errors: LCP_ERR_ARG for a negative size, NULL pointers (n > 0),
  * a bad range or stop table, or misalignment.  planes * rows * cols == 0 is a

@@ -18,11 +18,14 @@ may import this module.  It imports nothing from the GPU library.
 Readings (listed in DESIGN.md)
 ------------------------------
 R17 Colour map (the paper names none): a table of stops (t, r, g, b, a) with
-    t from 0 to 1; t = clamp((x - vmin) / (vmax - vmin), 0, 1); linear
-    interpolation inside the stop segment that holds t; byte =
-    floor(255 ch + 0.5).  NaN values get their own colour; an optional
-    crossing mask paints the mean-field contour cells in a contour colour
-    (the black / cyan contour of Fig. 1a / Fig. 3c at cell resolution).
+    t from 0 to 1; t = clamp((x - vmin) R, 0, 1) with R = 1 / (vmax - vmin);
+    linear interpolation inside the stop segment s that holds t, as
+    f = (t - t_s) r_s and ch = c_s + f d_s with r_s = 1 / (t_{s+1} - t_s) and
+    d_s = c_{s+1} - c_s formed once per table; byte = floor(255 ch + 0.5).
+    Every step is one fp32 operation rounded to nearest.  NaN values get their
+    own colour; an optional crossing mask paints the mean-field contour cells
+    in a contour colour (the black / cyan contour of Fig. 1a / Fig. 3c at cell
+    resolution).
 """
 
 from __future__ import annotations
@@ -58,18 +61,20 @@ def colormap_rgba(values, vmin: float, vmax: float, stops, nan_rgba: int = 0, ma
     st = np.asarray(stops, dtype=_F).reshape(-1, 5)
     n_stops = st.shape[0]
     lo, hi = _F(vmin), _F(vmax)
+    one = _F(1.0)
     with np.errstate(invalid="ignore", over="ignore"):
-        t = ((x - lo).astype(_F) / (hi - lo)).astype(_F)
-        t = np.minimum(np.maximum(t, _F(0.0)), _F(1.0))
+        big_r = one / (hi - lo)                               # R (0 when the range overflows)
+        r_seg = one / (st[1:, 0] - st[:-1, 0])                # r_s
+        d_seg = st[1:, 1:] - st[:-1, 1:]                      # d_s, [n_stops - 1, 4]
+        t = ((x - lo).astype(_F) * big_r).astype(_F)
+        t = np.fmin(np.fmax(t, _F(0.0)), _F(1.0))  # maxNum / minNum: a NaN operand yields the other
         s = np.zeros(x.shape, dtype=np.int64)
         for q in range(1, n_stops - 1):
             s = np.where(t >= st[q, 0], q, s)
-        a, b = st[s], st[s + 1]
-        f = ((t - a[..., 0]).astype(_F) / (b[..., 0] - a[..., 0]).astype(_F)).astype(_F)
+        f = ((t - st[s, 0]).astype(_F) * r_seg[s]).astype(_F)
         out = np.empty(x.shape + (4,), dtype=np.uint8)
         for ch in range(4):
-            d = (b[..., 1 + ch] - a[..., 1 + ch]).astype(_F)
-            c = (a[..., 1 + ch] + (f * d).astype(_F)).astype(_F)
+            c = (st[s, 1 + ch] + (f * d_seg[s, ch]).astype(_F)).astype(_F)
             out[..., ch] = _quantise(c)
     nan_bytes = np.array([(nan_rgba >> (8 * k)) & 0xFF for k in range(4)], dtype=np.uint8)
     out[np.isnan(x)] = nan_bytes

@@ -3,14 +3,17 @@
 // last paragraph) and clamps the mean-field divergence to a display range
 // before mapping it (Sec. 4.2, Fig. 3c); no graphics API is involved here.
 //
-// Every value costs 4 bytes read and 4 bytes written, so the kernel is a
-// plain stream: each thread maps 4 consecutive values (one 16-byte load and
-// one 16-byte store when the buffers allow it).  The colour stops are staged
-// in shared memory, so lanes that fall in different stop segments index them
-// without serialising on the constant cache.  Each channel is computed by a
-// fixed sequence of IEEE fp32 operations rounded to nearest (no contraction
-// into fused multiply-adds), which the header states, so the bytes do not
-// depend on the compiler.
+// Every value costs 4 bytes read and 4 bytes written, so the kernel must stay
+// under about 45 instructions per value to run at HBM speed.  Hence: each
+// thread maps 4 consecutive values (one 16-byte load and store when the
+// buffers allow it); the reciprocals and colour differences of every stop
+// segment are formed once per call on the host; the segment of a value is the
+// count of stop positions at or below it, compared against registers; the four
+// channels are interpolated and quantised as two float2 pairs with Blackwell's
+// paired fp32 instructions (each half an IEEE rounded-to-nearest operation, so
+// the bytes equal those of the scalar steps the header fixes); the row and
+// column of the mask bits advance with the grid stride instead of being
+// divided out, and one or two mask words serve a group of 4 values.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -22,51 +25,66 @@ namespace {
 
 constexpr int kCT = 256;  // threads per block
 
+struct Seg {  // one stop segment s: position, 1 / width, colour c_s, difference d_s
+    float t, r, pad0, pad1;
+    float4 c, d;
+};
+
 struct ColorParams {
     const float* x;
     const uint32_t* mask;
     uint32_t* rgba;
     int64_t n;        // values
-    int cols, rows;   // mask geometry: values are [planes][rows][cols]
+    int cols;         // values per mask row ([planes][rows][cols])
     int n_words;      // mask words per row
-    float vmin, vmax;
+    float vmin, big_r;
     uint32_t nan_rgba, mask_rgba;
-    int n_stops;
-    float stops[LCP_MAX_COLOR_STOPS * 5];
+    int n_seg;        // n_stops - 1
+    Seg seg[LCP_MAX_COLOR_STOPS - 1];
 };
 
-__device__ __forceinline__ uint32_t quantise(float ch) {
-    float b = floorf(__fadd_rn(__fmul_rn(ch, 255.0f), 0.5f));
-    b = fminf(fmaxf(b, 0.0f), 255.0f);
-    return (uint32_t)b;
-}
-
-__device__ __forceinline__ uint32_t map_one(const ColorParams& p, const float* st, float x) {
-    if (x != x) return p.nan_rgba;
-    float t = __fdiv_rn(__fsub_rn(x, p.vmin), __fsub_rn(p.vmax, p.vmin));
+template <int NT>  // NT >= n_stops - 2 interior stop positions, held in registers
+__device__ __forceinline__ uint32_t map_one(const ColorParams& p, const Seg* seg, const float (&thr)[NT], float x) {
+    float t = __fmul_rn(__fsub_rn(x, p.vmin), p.big_r);
     t = fminf(fmaxf(t, 0.0f), 1.0f);
     int s = 0;
-    for (int q = 1; q < p.n_stops - 1; ++q) s = t >= st[5 * q] ? q : s;
-    const float* a = st + 5 * s;
-    const float* b = a + 5;
-    const float f = __fdiv_rn(__fsub_rn(t, a[0]), __fsub_rn(b[0], a[0]));
-    uint32_t out = 0;
 #pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
-        const float c = __fadd_rn(a[1 + ch], __fmul_rn(f, __fsub_rn(b[1 + ch], a[1 + ch])));
-        out |= quantise(c) << (8 * ch);
-    }
-    return out;
+    for (int q = 0; q < NT; ++q) s += t >= thr[q] ? 1 : 0;  // unused entries hold 2 > t
+    const Seg& g = seg[s];
+    const float f = __fmul_rn(__fsub_rn(t, g.t), g.r);
+    const float2 ff = make_float2(f, f);
+    const float2 h = make_float2(255.0f, 255.0f), half = make_float2(0.5f, 0.5f);
+    const float2 rg = __fadd2_rn(__fmul2_rn(__fadd2_rn(make_float2(g.c.x, g.c.y), __fmul2_rn(ff, make_float2(g.d.x, g.d.y))), h), half);
+    const float2 ba = __fadd2_rn(__fmul2_rn(__fadd2_rn(make_float2(g.c.z, g.c.w), __fmul2_rn(ff, make_float2(g.d.z, g.d.w))), h), half);
+    // floor of values in [0.4999, 255.5001] (the clamp of the header never binds: f <= 1 + 2^-23 and
+    // the colours lie in [0, 1]), so the conversions cannot leave 0..255
+    const uint32_t r8 = __float2uint_rd(rg.x), g8 = __float2uint_rd(rg.y);
+    const uint32_t b8 = __float2uint_rd(ba.x), a8 = __float2uint_rd(ba.y);
+    const uint32_t c = r8 | (g8 << 8) | (b8 << 16) | (a8 << 24);
+    return x != x ? p.nan_rgba : c;
 }
 
-template <bool MASK, typename Idx>
+template <bool MASK, typename Idx, int NT>
 __global__ void __launch_bounds__(kCT) colormap_kernel(const __grid_constant__ ColorParams p) {
-    __shared__ float st[LCP_MAX_COLOR_STOPS * 5];
-    for (int q = threadIdx.x; q < p.n_stops * 5; q += kCT) st[q] = p.stops[q];
+    __shared__ Seg seg[LCP_MAX_COLOR_STOPS - 1];
+    for (int q = threadIdx.x; q < p.n_seg; q += kCT) seg[q] = p.seg[q];
+    float thr[NT];
+#pragma unroll
+    for (int q = 0; q < NT; ++q) thr[q] = q + 1 < p.n_seg ? p.seg[q + 1].t : 2.0f;
     __syncthreads();
     const bool vec = ((reinterpret_cast<uintptr_t>(p.x) | reinterpret_cast<uintptr_t>(p.rgba)) & 15) == 0;
     const Idx n = (Idx)p.n;
-    for (Idx g = ((Idx)blockIdx.x * kCT + threadIdx.x) * 4; g < n; g += (Idx)gridDim.x * kCT * 4) {
+    const Idx g0 = ((Idx)blockIdx.x * kCT + threadIdx.x) * 4, step = (Idx)gridDim.x * kCT * 4;
+    // mask position of the group's first value, advanced by the stride without division
+    int col = 0, dcol = 0;
+    Idx row = 0, drow = 0;
+    if (MASK) {
+        row = g0 / (Idx)p.cols;
+        col = (int)(g0 - row * (Idx)p.cols);
+        drow = step / (Idx)p.cols;
+        dcol = (int)(step - drow * (Idx)p.cols);
+    }
+    for (Idx g = g0; g < n; g += step) {
         float x[4];
         const int cnt = n - g >= 4 ? 4 : (int)(n - g);
         if (vec && cnt == 4) {
@@ -80,18 +98,35 @@ __global__ void __launch_bounds__(kCT) colormap_kernel(const __grid_constant__ C
         }
         uint32_t c[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) c[e] = map_one(p, st, x[e]);
-        if (MASK) {  // row and column of the first value; the next three follow along the row
-            const Idx rowg = g / (Idx)p.cols;
-            int col = (int)(g - rowg * (Idx)p.cols);
-            Idx row = rowg;
-            for (int e = 0; e < cnt; ++e) {
-                const uint32_t w = p.mask[(int64_t)row * p.n_words + (col >> 5)];
-                if (((w >> (col & 31)) & 1u) && x[e] == x[e]) c[e] = p.mask_rgba;  // NaN keeps its colour
-                if (++col == p.cols) {
-                    col = 0;
-                    ++row;
+        for (int e = 0; e < 4; ++e) c[e] = map_one<NT>(p, seg, thr, x[e]);
+        if (MASK) {
+            uint32_t bits;
+            if (col + cnt <= p.cols) {  // the group lies in one mask row: one or two words
+                const uint32_t* wp = p.mask + (int64_t)row * p.n_words + (col >> 5);
+                const int sh = col & 31;
+                uint64_t w2 = wp[0];
+                if (sh + cnt > 32) w2 |= (uint64_t)wp[1] << 32;
+                bits = (uint32_t)(w2 >> sh);
+            } else {  // the group wraps into the next row
+                bits = 0;
+                int cc = col;
+                Idx rr = row;
+                for (int e = 0; e < cnt; ++e) {
+                    bits |= ((p.mask[(int64_t)rr * p.n_words + (cc >> 5)] >> (cc & 31)) & 1u) << e;
+                    if (++cc == p.cols) {
+                        cc = 0;
+                        ++rr;
+                    }
                 }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (((bits >> e) & 1u) && x[e] == x[e]) c[e] = p.mask_rgba;  // NaN keeps its colour
+            col += dcol;
+            row += drow;
+            if (col >= p.cols) {
+                col -= p.cols;
+                ++row;
             }
         }
         if (vec && cnt == 4) {
@@ -100,6 +135,13 @@ __global__ void __launch_bounds__(kCT) colormap_kernel(const __grid_constant__ C
             for (int e = 0; e < cnt; ++e) p.rgba[g + e] = c[e];
         }
     }
+}
+
+template <bool MASK, typename Idx>
+void launch_nt(const ColorParams& p, int grid, cudaStream_t st) {
+    if (p.n_seg - 1 <= 2) colormap_kernel<MASK, Idx, 2><<<grid, kCT, 0, st>>>(p);
+    else if (p.n_seg - 1 <= 6) colormap_kernel<MASK, Idx, 6><<<grid, kCT, 0, st>>>(p);
+    else colormap_kernel<MASK, Idx, LCP_MAX_COLOR_STOPS - 2><<<grid, kCT, 0, st>>>(p);
 }
 
 }  // namespace
@@ -135,24 +177,44 @@ extern "C" lcp_status lcp_colormap(const float* values, int planes, int rows, in
     p.rgba = reinterpret_cast<uint32_t*>(rgba);
     p.n = n;
     p.cols = cols;
-    p.rows = rows;
     p.n_words = (cols + 31) / 32;
+    // the once-per-call terms, each one fp32 operation (volatile keeps the host
+    // compiler from contracting or widening them)
+    volatile float lo = vmin, hi = vmax;
+    volatile float range = hi - lo;
+    volatile float big_r = 1.0f / range;
     p.vmin = vmin;
-    p.vmax = vmax;
+    p.big_r = big_r;
     p.nan_rgba = nan_rgba;
     p.mask_rgba = mask_rgba;
-    p.n_stops = n_stops;
-    for (int q = 0; q < 5 * n_stops; ++q) p.stops[q] = stops[q];
+    p.n_seg = n_stops - 1;
+    for (int q = 0; q + 1 < n_stops; ++q) {
+        const float* a = stops + 5 * q;
+        const float* b = a + 5;
+        volatile float w = b[0] - a[0];
+        volatile float r = 1.0f / w;
+        Seg& sg = p.seg[q];
+        sg.t = a[0];
+        sg.r = r;
+        sg.pad0 = sg.pad1 = 0.0f;
+        float d[4];
+        for (int c = 0; c < 4; ++c) {
+            volatile float dc = b[1 + c] - a[1 + c];
+            d[c] = dc;
+        }
+        sg.c = make_float4(a[1], a[2], a[3], a[4]);
+        sg.d = make_float4(d[0], d[1], d[2], d[3]);
+    }
     const int64_t groups = (n + 3) / 4;
     const int grid = (int)std::min<int64_t>((groups + kCT - 1) / kCT, (int64_t)num_sms() * 8);
     cudaStream_t st = (cudaStream_t)stream;
     const bool small = n < (1ll << 31) - 4 * (int64_t)kCT * grid;
     if (mask) {
-        if (small) colormap_kernel<true, uint32_t><<<grid, kCT, 0, st>>>(p);
-        else colormap_kernel<true, int64_t><<<grid, kCT, 0, st>>>(p);
+        if (small) launch_nt<true, uint32_t>(p, grid, st);
+        else launch_nt<true, int64_t>(p, grid, st);
     } else {
-        if (small) colormap_kernel<false, uint32_t><<<grid, kCT, 0, st>>>(p);
-        else colormap_kernel<false, int64_t><<<grid, kCT, 0, st>>>(p);
+        if (small) launch_nt<false, uint32_t>(p, grid, st);
+        else launch_nt<false, int64_t>(p, grid, st);
     }
     return check_launch(fn);
 }

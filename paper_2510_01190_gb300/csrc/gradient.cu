@@ -33,6 +33,22 @@ __device__ __forceinline__ float ldm(const __nv_bfloat16* p) {
     return __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p)) << 16);
 }
 
+// Speed |(a, b)| with the hardware square root (relative error ~2^-22; the
+// speed-gradient path states FP32 accuracy, not correct rounding).  Every kernel
+// of this file uses it, so the fused and two-step paths agree bit for bit.
+__device__ __forceinline__ float speed_of(float a, float b) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(fmaf(a, a, b * b)));
+    return r;
+}
+__device__ __forceinline__ float2 speed_of2(float2 a, float2 b) {
+    const float2 q = __ffma2_rn(a, a, __fmul2_rn(b, b));
+    float2 r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r.x) : "f"(q.x));
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r.y) : "f"(q.y));
+    return r;
+}
+
 __device__ __forceinline__ void st_evict_last_f4(float4* p, float4 v) {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
@@ -84,7 +100,7 @@ __global__ void __launch_bounds__(kGW * 32, 2) grad_stats_kernel(const __grid_co
         }
         float s[kGR + 2];
 #pragma unroll
-        for (int q = 0; q < kGR + 2; ++q) s[q] = sqrtf(fmaf(a[q], a[q], b[q] * b[q]));
+        for (int q = 0; q < kGR + 2; ++q) s[q] = speed_of(a[q], b[q]);
 #pragma unroll
         for (int q = 0; q < kGR; ++q) {
             const float sc = s[q + 1];
@@ -120,6 +136,147 @@ __global__ void __launch_bounds__(kGW * 32, 2) grad_stats_kernel(const __grid_co
     }
 }
 
+// ---- paired variant: two columns per lane ------------------------------------
+// Lane l of a warp tile holds columns c0 - 2 + 2l and c0 - 1 + 2l (loaded as one
+// bf16x2 / float2), of vertex rows r0 - 1 .. r0 + 4; lanes 1..30 own the 60
+// vertex columns c0 .. c0 + 59.  Loads are clamped to the grid, which turns the
+// one-sided differences at the ends into the same subtraction with the scale
+// 1/dx (1/dy) instead of 1/(2dx): no selects per member.  Speeds, differences
+// and shifted sums run on float2 pairs (FFMA2 / FADD2 / FMUL2), and the next
+// member's loads are issued before the current member is processed.
+constexpr int kPR = 4;   // vertex rows per warp tile
+constexpr int kPC = 60;  // vertex columns per warp tile
+
+template <typename T>
+struct PairLd;
+template <>
+struct PairLd<float> {
+    using raw = float2;
+    static __device__ __forceinline__ raw ld(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+    static __device__ __forceinline__ raw ld2(const float* p0, const float* p1) { return make_float2(__ldg(p0), __ldg(p1)); }
+    static __device__ __forceinline__ float2 cvt(raw r) { return r; }
+};
+template <>
+struct PairLd<__nv_bfloat16> {
+    using raw = uint32_t;
+    static __device__ __forceinline__ raw ld(const __nv_bfloat16* p) { return __ldg(reinterpret_cast<const unsigned*>(p)); }
+    static __device__ __forceinline__ raw ld2(const __nv_bfloat16* p0, const __nv_bfloat16* p1) {
+        return (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p0)) |
+               ((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p1)) << 16);
+    }
+    static __device__ __forceinline__ float2 cvt(raw r) {
+        return make_float2(__uint_as_float(r << 16), __uint_as_float(r & 0xFFFF0000u));
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kGW * 32, 2) grad_stats_pair_kernel(const __grid_constant__ GradParams p) {
+    using L = PairLd<T>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c0 = (blockIdx.x * kGW + warp) * kPC;  // even
+    const int r0 = p.s0 + blockIdx.y * kPR;
+    if (c0 >= p.W || r0 > p.s1) return;              // uniform per warp; no block barriers below
+    const int H = p.H, W = p.W;
+    const int ca = c0 - 2 + 2 * lane;                // this lane's first column (even; W is even)
+    const bool inside = ca >= 0 && ca + 1 < W;       // both columns in the grid: one paired load
+    const int cal = min(max(ca, 0), W - 1), cbl = min(max(ca + 1, 0), W - 1);
+    const bool own = lane >= 1 && lane <= 30 && ca < W;
+    // x scales: the ends take the one-sided step (the clamped neighbour is the vertex itself)
+    const float2 kx = make_float2(ca == 0 ? p.sx1 : p.sx2, ca + 1 == W - 1 ? p.sx1 : p.sx2);
+    const int nr = min(kPR, p.s1 - r0 + 1);
+    int off[kPR + 2];  // rows r0-1 .. r0+kPR, clamped (H*W < 2^31)
+#pragma unroll
+    for (int q = 0; q < kPR + 2; ++q) off[q] = min(max(r0 - 1 + q, 0), H - 1) * W;
+    float ky[kPR];
+#pragma unroll
+    for (int q = 0; q < kPR; ++q) ky[q] = (r0 + q == 0 || r0 + q >= H - 1) ? p.sy1 : p.sy2;
+    const T* u = reinterpret_cast<const T*>(p.u);
+    const T* v = reinterpret_cast<const T*>(p.v);
+    auto load = [&](int m, typename L::raw (&ru)[kPR + 2], typename L::raw (&rv)[kPR + 2]) {
+        const T* um = u + (int64_t)m * p.stride;
+        const T* vm = v + (int64_t)m * p.stride;
+        if (inside) {
+#pragma unroll
+            for (int q = 0; q < kPR + 2; ++q) {
+                ru[q] = L::ld(um + off[q] + ca);
+                rv[q] = L::ld(vm + off[q] + ca);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kPR + 2; ++q) {
+                ru[q] = L::ld2(um + off[q] + cal, um + off[q] + cbl);
+                rv[q] = L::ld2(vm + off[q] + cal, vm + off[q] + cbl);
+            }
+        }
+    };
+    float2 x0x[kPR], x0y[kPR], s1x[kPR], s2x[kPR], s1y[kPR], s2y[kPR];
+    auto grads = [&](const typename L::raw (&ru)[kPR + 2], const typename L::raw (&rv)[kPR + 2], float2 (&gx)[kPR],
+                     float2 (&gy)[kPR]) {
+        float2 sp[kPR + 2];
+#pragma unroll
+        for (int q = 0; q < kPR + 2; ++q) sp[q] = speed_of2(L::cvt(ru[q]), L::cvt(rv[q]));
+#pragma unroll
+        for (int q = 0; q < kPR; ++q) {
+            const float2 sc = sp[q + 1];
+            const float sl = __shfl_up_sync(kFull, sc.y, 1);    // speed one column left of ca
+            const float sr = __shfl_down_sync(kFull, sc.x, 1);  // speed one column right of ca + 1
+            gx[q] = __fmul2_rn(__fadd2_rn(make_float2(sc.y, sr), make_float2(-sl, -sc.x)), kx);
+            gy[q] = __fmul2_rn(__fadd2_rn(sp[q + 2], make_float2(-sp[q].x, -sp[q].y)), make_float2(ky[q], ky[q]));
+        }
+    };
+    typename L::raw ru[kPR + 2], rv[kPR + 2], nu[kPR + 2], nv[kPR + 2];
+    load(0, ru, rv);
+    if (p.M > 1) load(1, nu, nv);
+    {
+        float2 gx[kPR], gy[kPR];
+        grads(ru, rv, gx, gy);
+#pragma unroll
+        for (int q = 0; q < kPR; ++q) {
+            x0x[q] = gx[q];
+            x0y[q] = gy[q];
+            s1x[q] = s2x[q] = s1y[q] = s2y[q] = make_float2(0.f, 0.f);
+        }
+    }
+    for (int m = 1; m < p.M; ++m) {
+#pragma unroll
+        for (int q = 0; q < kPR + 2; ++q) {
+            ru[q] = nu[q];
+            rv[q] = nv[q];
+        }
+        if (m + 1 < p.M) load(m + 1, nu, nv);
+        float2 gx[kPR], gy[kPR];
+        grads(ru, rv, gx, gy);
+#pragma unroll
+        for (int q = 0; q < kPR; ++q) {
+            const float2 dxv = __fadd2_rn(gx[q], make_float2(-x0x[q].x, -x0x[q].y));
+            const float2 dyv = __fadd2_rn(gy[q], make_float2(-x0y[q].x, -x0y[q].y));
+            s1x[q] = __fadd2_rn(s1x[q], dxv);
+            s2x[q] = __ffma2_rn(dxv, dxv, s2x[q]);
+            s1y[q] = __fadd2_rn(s1y[q], dyv);
+            s2y[q] = __ffma2_rn(dyv, dyv, s2y[q]);
+        }
+    }
+    if (!own) return;
+    const float fm = (float)p.M, fdof = (float)(p.M - p.ddof);
+    auto rec = [&](float x0, float a1, float a2) {
+        const float dl = a1 / fm;
+        const float vv = (a2 - a1 * dl) / fdof;
+        return make_float4(x0, dl, vv < 0.f ? 0.f : vv, 0.f);
+    };
+#pragma unroll
+    for (int q = 0; q < kPR; ++q) {
+        if (q < nr) {
+            const int64_t n = (int64_t)(r0 + q - p.row0) * W + ca;
+            st_evict_last_f4(p.st + n, rec(x0x[q].x, s1x[q].x, s2x[q].x));
+            st_evict_last_f4(p.st + p.ps + n, rec(x0y[q].x, s1y[q].x, s2y[q].x));
+            if (ca + 1 < W) {
+                st_evict_last_f4(p.st + n + 1, rec(x0x[q].y, s1x[q].y, s2x[q].y));
+                st_evict_last_f4(p.st + p.ps + n + 1, rec(x0y[q].y, s1y[q].y, s2y[q].y));
+            }
+        }
+    }
+}
+
 // gradient members: one thread per (member, vertex)
 template <typename T>
 __global__ void __launch_bounds__(256) grad_members_kernel(const T* __restrict__ u, const T* __restrict__ v,
@@ -134,8 +291,7 @@ __global__ void __launch_bounds__(256) grad_members_kernel(const T* __restrict__
         const T* vm = v + m * stride;
         auto speed = [&](int jj, int ii) {
             const int64_t o = (int64_t)jj * W + ii;
-            const float a = ldm(um + o), b = ldm(vm + o);
-            return sqrtf(fmaf(a, a, b * b));
+            return speed_of(ldm(um + o), ldm(vm + o));
         };
         const int il = max(i - 1, 0), ih = min(i + 1, W - 1), jl = max(j - 1, 0), jh = min(j + 1, H - 1);
         gx[q] = (speed(j, ih) - speed(j, il)) * (ih - il == 2 ? sx2 : sx1);
@@ -147,6 +303,9 @@ template <typename T>
 lcp_status run_grad(const void* u, const void* v, int M, int H, int W, int64_t stride, int ddof, double dx, double dy,
                     const float* iso, int K, void* out, lcp_dtype out_dtype, uint32_t* mask, void* ws,
                     cudaStream_t st) {
+    // paired loads need every row and member to start on an even column
+    const bool paired = W % 2 == 0 && stride % 2 == 0 && ((uintptr_t)u % (2 * sizeof(T))) == 0 &&
+                        ((uintptr_t)v % (2 * sizeof(T))) == 0;
     const WsGeometry G = ws_geometry(H, W);
     float4* rec = reinterpret_cast<float4*>(reinterpret_cast<char*>(ws) + G.ctr_bytes);
     const int64_t ps = (int64_t)(G.plane_bytes / sizeof(float4));
@@ -171,8 +330,13 @@ lcp_status run_grad(const void* u, const void* v, int M, int H, int W, int64_t s
         gp.sx2 = (float)(0.5 / dx);
         gp.sy1 = (float)(1.0 / dy);
         gp.sy2 = (float)(0.5 / dy);
-        const dim3 grid((W + kGW * kGC - 1) / (kGW * kGC), (s1 - s0 + 1 + kGR - 1) / kGR);
-        grad_stats_kernel<T><<<grid, kGW * 32, 0, st>>>(gp);
+        if (paired) {
+            const dim3 grid((W + kGW * kPC - 1) / (kGW * kPC), (s1 - s0 + 1 + kPR - 1) / kPR);
+            grad_stats_pair_kernel<T><<<grid, kGW * 32, 0, st>>>(gp);
+        } else {
+            const dim3 grid((W + kGW * kGC - 1) / (kGW * kGC), (s1 - s0 + 1 + kGR - 1) / kGR);
+            grad_stats_kernel<T><<<grid, kGW * 32, 0, st>>>(gp);
+        }
         lcp_status s = check_launch("lcp_speed_gradient_ws (statistics)");
         if (s != LCP_OK) return s;
         s = ws_lcp_rows(rec, ps, s0, H, W, r0, r1, dx, dy, iso, K, out, out_dtype, mask, st);
@@ -225,7 +389,7 @@ extern "C" lcp_status lcp_speed_gradient_ws(const void* u, const void* v, lcp_dt
     const WsGeometry G = ws_geometry(H, W);
     if (workspace_bytes < G.total)
         return fail(LCP_ERR_ARG, "%s: workspace too small (%zu < %zu bytes)", fn, workspace_bytes, G.total);
-    if ((H + 2 + kGR - 1) / kGR > 65535) return fail(LCP_ERR_UNSUPPORTED, "%s: H too large", fn);
+    if ((H + 2 + kPR - 1) / kPR > 65535) return fail(LCP_ERR_UNSUPPORTED, "%s: H too large", fn);
     const int64_t stride = M > 1 ? member_stride : (int64_t)H * W;
     cudaStream_t st = (cudaStream_t)stream;
     if (in_dtype == LCP_F32)

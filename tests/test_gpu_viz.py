@@ -88,6 +88,13 @@ def test_colormap_large_grid_stride(lib):
     assert np.array_equal(got, want)
 
 
+def test_colormap_overflowing_range(lib):
+    x = torch.tensor([[np.inf, -np.inf, 1.0, np.nan, 3e38]], dtype=torch.float32, device="cuda")
+    got = lib.lcp_colormap(x, -3e38, 3e38, lib.DEFAULT_STOPS, nan_rgba=7).cpu().numpy()
+    want = V.colormap_rgba(x.cpu().numpy(), -3e38, 3e38, lib.DEFAULT_STOPS, nan_rgba=7)
+    assert np.array_equal(got, want)
+
+
 def test_colormap_empty(lib):
     x = torch.empty((0, 5, 7), dtype=torch.float32, device="cuda")
     assert lib.lcp_colormap(x).shape == (0, 5, 7, 4)

@@ -77,3 +77,10 @@ def test_monotone_channel_is_non_decreasing():
     assert np.all(np.diff(got[:, 0].astype(int)) >= 0)
     assert x[0] < -2.0 and x[-1] > 2.0  # both clamped ends are reached
     assert got[0, 0] == 0 and got[-1, 0] == 255
+
+
+def test_overflowing_range_maps_infinities_like_maxnum():
+    """vmax - vmin overflows to inf, so R = 0 and x = +inf gives inf * 0 = NaN;
+    maxNum turns it into 0, so +inf takes the first stop's colour."""
+    got = V.colormap_rgba(np.array([np.inf, 1.0]), -3e38, 3e38, GREY)
+    assert list(got[0]) == [0, 0, 0, 0] and list(got[1]) == [0, 0, 0, 0]
