@@ -49,17 +49,20 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-mc", action="store_true", help="skip the Monte Carlo equal-error comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--workload", choices=["latlon", "batch", "learned", "ocean", "redsea", "colormap"],
+    ap.add_argument("--workload", choices=["latlon", "batch", "learned", "ocean", "redsea", "colormap", "volume"],
                     default="latlon",
                     help="latlon: the 721x1440 field (default); batch: 256 uneven fields in one persistent launch; "
                          "learned: the non-Gaussian surrogate; ocean: 8192^2 bf16; redsea: the speed-gradient "
-                         "preprocessing of the 8192^2 eddy field; colormap: RGBA8 of its LCP map")
+                         "preprocessing of the 8192^2 eddy field; colormap: RGBA8 of its LCP map; volume: 3D "
+                         "256^3 fields")
     ap.add_argument("--tile", type=str, default=None,
                     help="batch workload: force the tile shape ROWS,COLS instead of autotuning")
     ap.add_argument("--train-epochs", type=int, default=20, help="learned workload: training epochs (untimed)")
     ap.add_argument("--rows", type=int, default=8192,
                     help="ocean / redsea / colormap workloads: grid rows (8192 by default; fewer rows make small "
                          "profiling cases)")
+    ap.add_argument("--depth", type=int, default=256,
+                    help="volume workload: z-planes of the 256 x 256 x D volume (fewer make small profiling cases)")
     ap.add_argument("--fields", type=int, default=256,
                     help="batch workload: use the first N of its 256 field descriptors (small cases for profiling)")
     return ap.parse_args()
@@ -1069,6 +1072,71 @@ def colormap_arm(args):
     return _finish(torch, pg, line, rank)
 
 
+VOLUME_WORKLOAD = ("volume 256x256x256, 20 members fp32 of (u, v, w) (64 random 3D Fourier modes per component + "
+                   "log-normal noise), 4 isovalues; fused 3D closed-form LCP of the hexahedral cells (fp32 maps)")
+
+
+def volume_arm(args):
+    """3D fields (Sec. 5's extension): members of u, v, w -> LCP of every hexahedral cell."""
+    torch, lib, dev, world, rank, local, pg = gpu_setup()
+    from paper_2510_01190_gb300 import synth
+
+    vol = synth.fourier_volume_torch(rank, d=max(2, args.depth), device=dev)
+    u, v, w, iso = vol["u"], vol["v"], vol["w"], vol["isovalues"]
+    Mm, Dd, Hh, Ww = u.shape
+    Kk = len(iso)
+    cells = (Dd - 1) * (Hh - 1) * (Ww - 1)
+    out = torch.empty((Kk, Dd - 1, Hh - 1, Ww - 1), dtype=torch.float32, device=dev)
+
+    def step():
+        lib.lcp3d_fused_ws(u, v, w, iso, out=out)
+
+    total_ms, kern_ms, clocks = timed_steps(torch, step, args.steps, args.warmup, local, pg, dev)
+    n = args.steps
+    ms_per_step = total_ms / n
+    value = weak_scaling_value(cells, world, ms_per_step)
+    alg = 3 * Mm * Dd * Hh * Ww * 4 + Kk * cells * 4
+    peak, peak_kind = measured_hbm_peak()
+    achieved = alg / (kern_ms / 1e3) / 1e9
+    ring_planes = max(4, (48 << 20) // (Hh * Ww * 48))
+    slabs = -(-Dd // max(1, min(ring_planes, Dd + 3) - 3))
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": profiled_traffic("lcp3d_fused_ws_256cubed_m20_k4.md", ("volume.cu", "lcp_common.cuh")),
+            "peak_kind": peak_kind,
+            "kernel": "lcp3d_fused_ws step: stats3_kernel<float> + lcp3_kernel<4,nomask,float> per slab of z-planes",
+            "alg_bytes_per_launch": alg, "kernel_ms": round(kern_ms, 4)}
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        from oracle import volume as V3
+
+        planes, cells_done, nb, t0 = 6, 0, 0, time.perf_counter()
+        while time.perf_counter() - t0 < 12.0:
+            z0 = (nb * 37) % (Dd - planes)
+            crop = lambda t: t[:, z0:z0 + planes].float().cpu().numpy()  # noqa: E731
+            V3.lcp_closed_form_3d(crop(u), crop(v), crop(w), 1.0, 1.0, 1.0, iso)
+            cells_done += (planes - 1) * (Hh - 1) * (Ww - 1)
+            nb += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": cells_done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nb} slabs of {planes} planes x {Hh} x {Ww} x {Mm} members, K={Kk} (FP64 numpy, one thread)",
+               "seconds": round(dt, 2)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": VOLUME_WORKLOAD if Dd == 256 else f"{Dd} planes of: " + VOLUME_WORKLOAD, "D": Dd,
+                   "H": Hh, "W": Ww, "M": Mm, "K": Kk, "global_batch": world,
+                   "parallelism": f"independent volumes x{world}" if world > 1 else "single",
+                   "l2": f"no flush: inputs {3 * Mm * Dd * Hh * Ww * 4 / 1e9:.1f} GB > 129 MB L2",
+                   "lcp_values_per_s": value * Kk, "hbm_frac_of_measured": roof["frac"]},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": None,
+        "e2e_note": "not measured for this line: 4 GB of members per step would be pinned on the host",
+        "clocks": clocks, "gpu_launches": 2 * slabs * n, "gpu": torch.cuda.get_device_name(dev),
+    }
+    return _finish(torch, pg, line, rank)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1083,6 +1151,8 @@ def main():
         return redsea_arm(args)
     if args.workload == "colormap":
         return colormap_arm(args)
+    if args.workload == "volume":
+        return volume_arm(args)
     return our_arm(args)
 
 

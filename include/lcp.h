@@ -452,6 +452,58 @@ lcp_status lcp_speed_gradient_ws(const void* u, const void* v, lcp_dtype in_dtyp
                                  size_t workspace_bytes, lcp_stream_t stream);
 
 /*
+ * 3D vector fields.  Sec. 5 names 3D fields as the next step; the closed form
+ * carries over term by term.  A volume has D planes (z, index k) of H rows (y,
+ * j) of W columns (x, i); element (m, k, j, i) of u lives at
+ * u[m * member_stride + (k * H + j) * W + i], member_stride >= D*H*W; u is the
+ * x, v the y and w the z component.  Eq. 1 gains (w[k+] - w[k-]) / ((k+ - k-) dz)
+ * with the same one-sided rule on every face; Eqs. 2/3 gain the matching terms.
+ * Cell (i, j, k) has the 8 vertices (i..i+1, j..j+1, k..k+1) and
+ *   LCP = 1 - prod_8 P(D < c) - prod_8 P(D >= c).
+ * Maps are [K][D-1][H-1][W-1]; masks [K][D-1][H-1][ceil((W-1)/32)] words with
+ * bit (i % 32) of word i / 32 set iff the mean-field cell crosses.
+ */
+
+/* Workspace bytes of lcp3d_fused_ws: a ring of z-planes of statistics records
+ * (48 bytes per vertex) sized to stay in L2 where the planes allow it. */
+size_t lcp3d_workspace_bytes(int M, int D, int H, int W, lcp_dtype in_dtype);
+
+/*
+ * lcp3d_fused_ws - members of (u, v, w) -> the 3D LCP map (and mask): FP32
+ * shifted-sum statistics per vertex (read once), the 3D divergence Gaussian and
+ * the LCP of every hexahedral cell and isovalue.
+ *   u, v, w    device members (LCP_F32 or LCP_BF16), layout above
+ *   M, D, H, W, member_stride, ddof, dx, dy, dz   as for the 2D calls
+ *   iso        HOST, 1 <= K <= LCP_MAX_ISOVALUES (passes of up to 8)
+ *   lcp_out    device [K][D-1][H-1][W-1] of out_dtype (LCP_F32 or LCP_F16)
+ *   mask       optional device words (layout above, cleared by the call) or NULL
+ *   workspace  device, 256-byte aligned, >= lcp3d_workspace_bytes
+ * Errors: LCP_ERR_ARG for NULL pointers, D, H or W < 2, M - ddof < 1, a small
+ * member_stride or workspace, dx, dy or dz <= 0, a bad dtype or K.
+ */
+lcp_status lcp3d_fused_ws(const void* u, const void* v, const void* w, lcp_dtype in_dtype, int M, int D, int H,
+                          int W, int64_t member_stride, int ddof, double dx, double dy, double dz, const float* iso,
+                          int K, void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, void* workspace,
+                          size_t workspace_bytes, lcp_stream_t stream);
+
+/*
+ * lcp3d_divergence - the 3D divergence Gaussian at every vertex from per-vertex
+ * statistics (device fp32 [D][H][W] each, e.g. from lcp_stats on (u, v) and on
+ * (w, w)); outputs mu_d, var_d device fp32 [D][H][W].
+ */
+lcp_status lcp3d_divergence(const float* mu_u, const float* var_u, const float* mu_v, const float* var_v,
+                            const float* mu_w, const float* var_w, int D, int H, int W, double dx, double dy,
+                            double dz, float* mu_d, float* var_d, lcp_stream_t stream);
+
+/*
+ * lcp3d_map - the LCP of every hexahedral cell from the divergence Gaussians
+ * (device fp32 [D][H][W]); iso HOST, 1 <= K <= 64; lcp_out and mask as above
+ * (the mask is written, not accumulated).
+ */
+lcp_status lcp3d_map(const float* mu_d, const float* var_d, int D, int H, int W, const float* iso, int K,
+                     void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, lcp_stream_t stream);
+
+/*
  * lcp_colormap - colour mapping of a scalar map into a headless RGBA8 buffer.
  * Sec. 3.1 (last paragraph) shows the LCP map by colour mapping, and Sec. 4.2
  * clamps the mean-field divergence to a display range before mapping it

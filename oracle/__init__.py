@@ -26,9 +26,13 @@ hand-evaluated networks, a finite-difference gradient check and Adam's
 first-step property.  ``viz`` (the colour map and the isocontour segments)
 is pinned by ``tests/test_oracle_viz.py``: exact integer byte formulas on dyadic
 inputs, the stops' own colours, special values, and marching squares against
-hand-drawn cases and the crossing mask.
+hand-drawn cases and the crossing mask.  ``volume`` (the 3D extension) is
+pinned by ``tests/test_oracle_volume.py``: exactness on linear fields, exact
+rational arithmetic, the reduction of z-invariant fields to the 2D oracle, axis
+permutation, and brute-force sampling with an independent generator.
 """
 
 from .lcp_oracle import *  # noqa: F401,F403
 from . import surrogate  # noqa: F401,E402
 from . import viz  # noqa: F401,E402
+from . import volume  # noqa: F401,E402

@@ -40,6 +40,10 @@ __all__ = [
     "lcp_philox_fill",
     "lcp_exact_empirical",
     "lcp_colormap",
+    "lcp3d_fused_ws",
+    "lcp3d_workspace_bytes",
+    "lcp3d_divergence",
+    "lcp3d_map",
     "lcp_speed_gradient",
     "lcp_speed_gradient_ws",
     "DEFAULT_STOPS",
@@ -112,6 +116,11 @@ _SIGNATURES = {
     "lcp_batch_autotune": (c_int, [ctypes.POINTER(lcp_batch_plan), c_int, ctypes.POINTER(lcp_tune), c_fp, c_vp]),
     "lcp_exact_empirical": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_double, c_double, c_fp, c_int,
                                     c_vp, c_vp, c_vp]),
+    "lcp3d_workspace_bytes": (ctypes.c_size_t, [c_int, c_int, c_int, c_int, c_int]),
+    "lcp3d_fused_ws": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double,
+                               c_double, c_fp, c_int, c_vp, c_int, c_vp, c_vp, ctypes.c_size_t, c_vp]),
+    "lcp3d_divergence": (c_int, [c_vp] * 6 + [c_int, c_int, c_int, c_double, c_double, c_double, c_vp, c_vp, c_vp]),
+    "lcp3d_map": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_fp, c_int, c_vp, c_int, c_vp, c_vp]),
     "lcp_speed_gradient": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_double, c_double, c_vp, c_vp,
                                    c_vp]),
     "lcp_speed_gradient_ws": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double,
@@ -347,6 +356,78 @@ def lcp_speed_gradient_ws(u, v, isovalues, dx: float = 1.0, dy: float = 1.0, ddo
     _check(lib.lcp_speed_gradient_ws(_ptr(u), _ptr(v), _dtype_code(u.dtype), m, h, w, stride, ddof, float(dx),
                                      float(dy), iso_p, k, _ptr(out), _dtype_code(out.dtype), _ptr(mask_out),
                                      c_vp(ws_ptr), ws_bytes, _stream()))
+    return out, mask_out
+
+
+def _members3(u, v, w):
+    if u.dim() != 4 or u.shape != v.shape or u.shape != w.shape or u.dtype != v.dtype or u.dtype != w.dtype:
+        raise ValueError("u, v and w must be [M, D, H, W] tensors of one shape and dtype")
+    if not (u.is_cuda and v.is_cuda and w.is_cuda):
+        raise ValueError("members must be CUDA tensors")
+    m, d, h, wd = u.shape
+    for t in (u, v, w):
+        if t.stride(3) != 1 or t.stride(2) != wd or t.stride(1) != h * wd:
+            raise ValueError("each member volume must be contiguous [D][H][W]")
+    if u.stride(0) != v.stride(0) or u.stride(0) != w.stride(0):
+        raise ValueError("u, v and w must share one member stride")
+    return m, d, h, wd, u.stride(0) if m > 1 else d * h * wd
+
+
+def lcp3d_workspace_bytes(m: int, d: int, h: int, w: int, dtype=torch.float32) -> int:
+    return int(load().lcp3d_workspace_bytes(m, d, h, w, _dtype_code(dtype)))
+
+
+def lcp3d_fused_ws(u, v, w, isovalues, dx: float = 1.0, dy: float = 1.0, dz: float = 1.0, ddof: int = 1,
+                   out_dtype=torch.float32, mask: bool = False, out=None, mask_out=None, workspace=None):
+    """3D members [M, D, H, W] of (u, v, w) -> LCP map [K, D-1, H-1, W-1] of the
+    hexahedral cells (and mean-field mask words [K, D-1, H-1, ceil((W-1)/32)]).
+    Returns (lcp, mask_words|None)."""
+    m, d, h, wd, stride = _members3(u, v, w)
+    iso, k, iso_p = _iso(isovalues)
+    if out is None:
+        out = torch.empty((k, d - 1, h - 1, wd - 1), dtype=out_dtype, device=u.device)
+    if mask and mask_out is None:
+        mask_out = torch.empty((k, d - 1, h - 1, mask_words_per_row(wd)), dtype=torch.int32, device=u.device)
+    mask_out = mask_out if mask else None
+    lib = load()
+    need = int(lib.lcp3d_workspace_bytes(m, d, h, wd, _dtype_code(u.dtype)))
+    if workspace is None:
+        _, ws_ptr = _workspace(need, u.device)
+        ws_bytes = need
+    else:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    _check(lib.lcp3d_fused_ws(_ptr(u), _ptr(v), _ptr(w), _dtype_code(u.dtype), m, d, h, wd, stride, ddof,
+                              float(dx), float(dy), float(dz), iso_p, k, _ptr(out), _dtype_code(out.dtype),
+                              _ptr(mask_out), c_vp(ws_ptr), ws_bytes, _stream()))
+    return out, mask_out
+
+
+def lcp3d_divergence(mu_u, var_u, mu_v, var_v, mu_w, var_w, dx: float = 1.0, dy: float = 1.0, dz: float = 1.0):
+    """3D divergence Gaussian at every vertex from fp32 [D, H, W] statistics: returns (mu_d, var_d)."""
+    shape = mu_u.shape
+    for t in (mu_u, var_u, mu_v, var_v, mu_w, var_w):
+        if t.dtype != torch.float32 or not t.is_cuda or t.shape != shape or not t.is_contiguous() or t.dim() != 3:
+            raise ValueError("statistics must be contiguous float32 CUDA tensors [D, H, W] of one shape")
+    mu_d, var_d = torch.empty_like(mu_u), torch.empty_like(mu_u)
+    d, h, w = shape
+    _check(load().lcp3d_divergence(*map(_ptr, (mu_u, var_u, mu_v, var_v, mu_w, var_w)), d, h, w, float(dx),
+                                   float(dy), float(dz), _ptr(mu_d), _ptr(var_d), _stream()))
+    return mu_d, var_d
+
+
+def lcp3d_map(mu_d, var_d, isovalues, out_dtype=torch.float32, mask: bool = False):
+    """LCP of every hexahedral cell from the divergence Gaussians [D, H, W]:
+    returns (lcp [K, D-1, H-1, W-1], mask_words|None)."""
+    for t in (mu_d, var_d):
+        if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 3 or not t.is_contiguous() or t.shape != mu_d.shape:
+            raise ValueError("mu_d and var_d must be contiguous float32 CUDA tensors [D, H, W]")
+    d, h, w = mu_d.shape
+    iso, k, iso_p = _iso(isovalues)
+    out = torch.empty((k, d - 1, h - 1, w - 1), dtype=out_dtype, device=mu_d.device)
+    mask_out = torch.empty((k, d - 1, h - 1, mask_words_per_row(w)), dtype=torch.int32, device=mu_d.device) \
+        if mask else None
+    _check(load().lcp3d_map(_ptr(mu_d), _ptr(var_d), d, h, w, iso_p, k, _ptr(out), _dtype_code(out.dtype),
+                            _ptr(mask_out), _stream()))
     return out, mask_out
 
 

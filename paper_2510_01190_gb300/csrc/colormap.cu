@@ -43,8 +43,18 @@ struct ColorParams {
     Seg seg[LCP_MAX_COLOR_STOPS - 1];
 };
 
-template <int NT>  // NT >= n_stops - 2 interior stop positions, held in registers
-__device__ __forceinline__ uint32_t map_one(const ColorParams& p, const Seg* seg, const float (&thr)[NT], float x) {
+// Paired add rounded toward minus infinity (add.rm.f32x2).
+__device__ __forceinline__ float2 fadd2_rm(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "add.rm.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
+template <int NT, int NA>  // NT >= n_stops - 2 interior stop positions, held in registers
+__device__ __forceinline__ uint32_t map_one(const ColorParams& p, const Seg* seg, const float (&thr)[NA], float x) {
     float t = __fmul_rn(__fsub_rn(x, p.vmin), p.big_r);
     t = fminf(fmaxf(t, 0.0f), 1.0f);
     int s = 0;
@@ -56,11 +66,14 @@ __device__ __forceinline__ uint32_t map_one(const ColorParams& p, const Seg* seg
     const float2 h = make_float2(255.0f, 255.0f), half = make_float2(0.5f, 0.5f);
     const float2 rg = __fadd2_rn(__fmul2_rn(__fadd2_rn(make_float2(g.c.x, g.c.y), __fmul2_rn(ff, make_float2(g.d.x, g.d.y))), h), half);
     const float2 ba = __fadd2_rn(__fmul2_rn(__fadd2_rn(make_float2(g.c.z, g.c.w), __fmul2_rn(ff, make_float2(g.d.z, g.d.w))), h), half);
-    // floor of values in [0.4999, 255.5001] (the clamp of the header never binds: f <= 1 + 2^-23 and
-    // the colours lie in [0, 1]), so the conversions cannot leave 0..255
-    const uint32_t r8 = __float2uint_rd(rg.x), g8 = __float2uint_rd(rg.y);
-    const uint32_t b8 = __float2uint_rd(ba.x), a8 = __float2uint_rd(ba.y);
-    const uint32_t c = r8 | (g8 << 8) | (b8 << 16) | (a8 << 24);
+    // floor of y in [0.4999, 255.5001] (the clamp of the header never binds: f <= 1 + 2^-23 and the
+    // colours lie in [0, 1]): y + 2^23 rounded down is 2^23 + floor(y) exactly, so the low byte of its
+    // bit pattern is the channel byte; three byte permutes pack r, g, b, a
+    const float2 kb = fadd2_rm(rg, make_float2(8388608.0f, 8388608.0f));
+    const float2 kc = fadd2_rm(ba, make_float2(8388608.0f, 8388608.0f));
+    const uint32_t lo = __byte_perm(__float_as_uint(kb.x), __float_as_uint(kb.y), 0x0040);
+    const uint32_t hi = __byte_perm(__float_as_uint(kc.x), __float_as_uint(kc.y), 0x0040);
+    const uint32_t c = __byte_perm(lo, hi, 0x5410);
     return x != x ? p.nan_rgba : c;
 }
 
@@ -68,7 +81,7 @@ template <bool MASK, typename Idx, int NT>
 __global__ void __launch_bounds__(kCT) colormap_kernel(const __grid_constant__ ColorParams p) {
     __shared__ Seg seg[LCP_MAX_COLOR_STOPS - 1];
     for (int q = threadIdx.x; q < p.n_seg; q += kCT) seg[q] = p.seg[q];
-    float thr[NT];
+    float thr[NT > 0 ? NT : 1];
 #pragma unroll
     for (int q = 0; q < NT; ++q) thr[q] = q + 1 < p.n_seg ? p.seg[q + 1].t : 2.0f;
     __syncthreads();
@@ -139,8 +152,11 @@ __global__ void __launch_bounds__(kCT) colormap_kernel(const __grid_constant__ C
 
 template <bool MASK, typename Idx>
 void launch_nt(const ColorParams& p, int grid, cudaStream_t st) {
-    if (p.n_seg - 1 <= 2) colormap_kernel<MASK, Idx, 2><<<grid, kCT, 0, st>>>(p);
-    else if (p.n_seg - 1 <= 6) colormap_kernel<MASK, Idx, 6><<<grid, kCT, 0, st>>>(p);
+    const int interior = p.n_seg - 1;  // stop positions strictly inside (0, 1)
+    if (interior == 0) colormap_kernel<MASK, Idx, 0><<<grid, kCT, 0, st>>>(p);
+    else if (interior <= 2) colormap_kernel<MASK, Idx, 2><<<grid, kCT, 0, st>>>(p);
+    else if (interior <= 4) colormap_kernel<MASK, Idx, 4><<<grid, kCT, 0, st>>>(p);
+    else if (interior <= 6) colormap_kernel<MASK, Idx, 6><<<grid, kCT, 0, st>>>(p);
     else colormap_kernel<MASK, Idx, LCP_MAX_COLOR_STOPS - 2><<<grid, kCT, 0, st>>>(p);
 }
 

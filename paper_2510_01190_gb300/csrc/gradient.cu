@@ -49,6 +49,16 @@ __device__ __forceinline__ float2 speed_of2(float2 a, float2 b) {
     return r;
 }
 
+// Paired subtraction a - b (sub.rn.f32x2): each half one IEEE operation.
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 __device__ __forceinline__ void st_evict_last_f4(float4* p, float4 v) {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
@@ -210,8 +220,8 @@ __global__ void __launch_bounds__(kGW * 32, 2) grad_stats_pair_kernel(const __gr
         }
     };
     float2 x0x[kPR], x0y[kPR], s1x[kPR], s2x[kPR], s1y[kPR], s2y[kPR];
-    auto grads = [&](const typename L::raw (&ru)[kPR + 2], const typename L::raw (&rv)[kPR + 2], float2 (&gx)[kPR],
-                     float2 (&gy)[kPR]) {
+    using raw_t = typename L::raw;
+    auto grads = [&](const raw_t (&ru)[kPR + 2], const raw_t (&rv)[kPR + 2], float2 (&gx)[kPR], float2 (&gy)[kPR]) {
         float2 sp[kPR + 2];
 #pragma unroll
         for (int q = 0; q < kPR + 2; ++q) sp[q] = speed_of2(L::cvt(ru[q]), L::cvt(rv[q]));
@@ -220,16 +230,30 @@ __global__ void __launch_bounds__(kGW * 32, 2) grad_stats_pair_kernel(const __gr
             const float2 sc = sp[q + 1];
             const float sl = __shfl_up_sync(kFull, sc.y, 1);    // speed one column left of ca
             const float sr = __shfl_down_sync(kFull, sc.x, 1);  // speed one column right of ca + 1
-            gx[q] = __fmul2_rn(__fadd2_rn(make_float2(sc.y, sr), make_float2(-sl, -sc.x)), kx);
-            gy[q] = __fmul2_rn(__fadd2_rn(sp[q + 2], make_float2(-sp[q].x, -sp[q].y)), make_float2(ky[q], ky[q]));
+            gx[q] = __fmul2_rn(fsub2(make_float2(sc.y, sr), make_float2(sl, sc.x)), kx);
+            gy[q] = __fmul2_rn(fsub2(sp[q + 2], sp[q]), make_float2(ky[q], ky[q]));
         }
     };
-    typename L::raw ru[kPR + 2], rv[kPR + 2], nu[kPR + 2], nv[kPR + 2];
-    load(0, ru, rv);
-    if (p.M > 1) load(1, nu, nv);
-    {
+    auto accumulate = [&](const raw_t (&ru)[kPR + 2], const raw_t (&rv)[kPR + 2]) {
         float2 gx[kPR], gy[kPR];
         grads(ru, rv, gx, gy);
+#pragma unroll
+        for (int q = 0; q < kPR; ++q) {
+            const float2 dxv = fsub2(gx[q], x0x[q]), dyv = fsub2(gy[q], x0y[q]);
+            s1x[q] = __fadd2_rn(s1x[q], dxv);
+            s2x[q] = __ffma2_rn(dxv, dxv, s2x[q]);
+            s1y[q] = __fadd2_rn(s1y[q], dyv);
+            s2y[q] = __ffma2_rn(dyv, dyv, s2y[q]);
+        }
+    };
+    // two load buffers in ping-pong: the next member's loads are in flight
+    // while the current one is processed, without register copies
+    raw_t au[kPR + 2], av[kPR + 2], bu[kPR + 2], bv[kPR + 2];
+    load(0, au, av);
+    if (p.M > 1) load(1, bu, bv);
+    {
+        float2 gx[kPR], gy[kPR];
+        grads(au, av, gx, gy);
 #pragma unroll
         for (int q = 0; q < kPR; ++q) {
             x0x[q] = gx[q];
@@ -237,25 +261,14 @@ __global__ void __launch_bounds__(kGW * 32, 2) grad_stats_pair_kernel(const __gr
             s1x[q] = s2x[q] = s1y[q] = s2y[q] = make_float2(0.f, 0.f);
         }
     }
-    for (int m = 1; m < p.M; ++m) {
-#pragma unroll
-        for (int q = 0; q < kPR + 2; ++q) {
-            ru[q] = nu[q];
-            rv[q] = nv[q];
-        }
-        if (m + 1 < p.M) load(m + 1, nu, nv);
-        float2 gx[kPR], gy[kPR];
-        grads(ru, rv, gx, gy);
-#pragma unroll
-        for (int q = 0; q < kPR; ++q) {
-            const float2 dxv = __fadd2_rn(gx[q], make_float2(-x0x[q].x, -x0x[q].y));
-            const float2 dyv = __fadd2_rn(gy[q], make_float2(-x0y[q].x, -x0y[q].y));
-            s1x[q] = __fadd2_rn(s1x[q], dxv);
-            s2x[q] = __ffma2_rn(dxv, dxv, s2x[q]);
-            s1y[q] = __fadd2_rn(s1y[q], dyv);
-            s2y[q] = __ffma2_rn(dyv, dyv, s2y[q]);
-        }
+    int m = 1;
+    for (; m + 1 < p.M; m += 2) {  // b holds member m
+        load(m + 1, au, av);
+        accumulate(bu, bv);
+        if (m + 2 < p.M) load(m + 2, bu, bv);
+        accumulate(au, av);
     }
+    if (m < p.M) accumulate(bu, bv);
     if (!own) return;
     const float fm = (float)p.M, fdof = (float)(p.M - p.ddof);
     auto rec = [&](float x0, float a1, float a2) {

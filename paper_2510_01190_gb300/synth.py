@@ -20,6 +20,8 @@ for their shapes:
 * ``non_gaussian_ensemble``  1024^2, 50 members: Fourier mean field with
   skew-normal or two-component Gaussian-mixture noise per vertex.
 * ``batch_descriptors``  256 fields of uneven size for the batched launch.
+* ``fourier_volume_torch``  3D volumes (256^3, 20 members by default) of random
+  3D Fourier modes plus log-normal noise levels, made on a torch device.
 """
 
 from __future__ import annotations
@@ -39,6 +41,7 @@ __all__ = [
     "batch_descriptors",
     "fourier_batch_torch",
     "mlp_init_params",
+    "fourier_volume_torch",
 ]
 
 
@@ -394,3 +397,61 @@ def mlp_init_params(seed: int = 0, n_in: int = 17, hidden: int = 64, zero_output
     if zero_output:
         p["w3"][:] = 0.0
     return p
+
+
+# ---------------------------------------------------------------------------
+# 3D volumes: random Fourier modes (made on a torch device)
+# ---------------------------------------------------------------------------
+def fourier_volume_torch(seed: int = 0, d: int = 256, h: int = 256, w: int = 256, m: int = 20, k: int = 4,
+                         n_modes: int = 64, kmax: int = 12, rms: float = 1.0, noise_median: float = 0.1,
+                         noise_shape: float = 0.5, device="cuda", dtype=None):
+    """3D ensemble: each of u, v, w a sum of ``n_modes`` modes
+    a cos(2 pi (kx x / W + ky y / H + kz z / D) + phi) with random integer
+    wavevectors 0 < |k| <= kmax and amplitude |k|^(-11/6) (energy ~ k^(-5/3)
+    in 3D), scaled to RMS ``rms``; every member adds Gaussian noise whose
+    per-vertex, per-component sigma is log-normal (median ``noise_median``).
+    ``k`` isovalues sit at evenly spaced percentiles from the 5th to the 95th of
+    the analytic divergence of the base field (the derivative of the series
+    itself, unit spacing), taken on a strided subsample.
+
+    returns dict(u, v, w [m, d, h, w] torch tensors; dx = dy = dz = 1; isovalues np.float32 [k])
+    """
+    import torch
+
+    if dtype is None:
+        dtype = torch.float32
+    g = _rng(seed, 7)
+    z = torch.arange(d, device=device, dtype=torch.float32)[:, None, None] / d
+    y = torch.arange(h, device=device, dtype=torch.float32)[None, :, None] / h
+    x = torch.arange(w, device=device, dtype=torch.float32)[None, None, :] / w
+    vecs = [(a, b, c) for a in range(-kmax, kmax + 1) for b in range(-kmax, kmax + 1) for c in range(-kmax, kmax + 1)
+            if 0 < a * a + b * b + c * c <= kmax * kmax]
+    base, div = [], torch.zeros((d, h, w), device=device, dtype=torch.float32)
+    for comp in range(3):
+        f = torch.zeros((d, h, w), device=device, dtype=torch.float32)
+        df = torch.zeros((d, h, w), device=device, dtype=torch.float32)
+        for q in g.choice(len(vecs), size=n_modes, replace=False):
+            kx, ky, kz = vecs[q]
+            amp = (kx * kx + ky * ky + kz * kz) ** (-11.0 / 12.0)
+            phase = g.uniform(0.0, 2.0 * math.pi)
+            theta = 2.0 * math.pi * (kx * x + ky * y + kz * z) + phase
+            f += amp * torch.cos(theta)
+            # derivative along this component's own axis (x for u, y for v, z for w), per grid step
+            kk, n = ((kx, w), (ky, h), (kz, d))[comp]
+            df += -amp * (2.0 * math.pi * kk / n) * torch.sin(theta)
+        scale = rms / float(torch.sqrt(torch.mean(f * f)))
+        base.append(f * scale)
+        div += df * scale
+    tg = torch.Generator(device=device)
+    tg.manual_seed(int(seed) * 7919 + 3)
+    comps = []
+    for comp in range(3):
+        sig = noise_median * torch.exp(noise_shape * torch.randn((d, h, w), generator=tg, device=device))
+        out = torch.empty((m, d, h, w), dtype=dtype, device=device)
+        for i in range(m):
+            out[i] = (base[comp] + sig * torch.randn((d, h, w), generator=tg, device=device)).to(dtype)
+        comps.append(out)
+    sample = div.reshape(-1)[:: max(1, div.numel() // 1000003)].double().cpu().numpy()
+    iso = np.percentile(sample, np.linspace(5, 95, k)).astype(np.float32) if k > 1 else \
+        np.array([np.median(sample)], np.float32)
+    return dict(u=comps[0], v=comps[1], w=comps[2], dx=1.0, dy=1.0, dz=1.0, isovalues=iso)

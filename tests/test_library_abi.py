@@ -134,3 +134,29 @@ def test_speed_gradient_rejects_bad_arguments(clib):
     assert f(*args, ctypes.c_void_p(520), 1 << 30, None) == -1 and "aligned" in _err(clib)
     big = [FAKE, FAKE, 0, 2, 65536, 32768, 65536 * 32768, 1, 1.0, 1.0, iso, 2, FAKE, 0, None]
     assert f(*big, ctypes.c_void_p(512), 1 << 40, None) == -3 and "2^31" in _err(clib)
+
+
+def test_volume_calls_reject_bad_arguments(clib):
+    iso = (ctypes.c_float * 2)(0.0, 1.0)
+    f = clib.lcp3d_fused_ws
+    ws = ctypes.c_void_p(512)
+    ok = [FAKE, FAKE, FAKE, 0, 4, 5, 6, 7, 5 * 6 * 7, 1, 1.0, 1.0, 1.0, iso, 2, FAKE, 0, None]
+    assert clib.lcp3d_workspace_bytes(4, 5, 6, 7, 0) > 0 and clib.lcp3d_workspace_bytes(4, 1, 6, 7, 0) == 0
+    bad = list(ok)
+    bad[2] = None
+    assert f(*bad, ws, 1 << 30, None) == -1 and "non-NULL" in _err(clib)
+    bad = list(ok)
+    bad[5] = 1
+    assert f(*bad, ws, 1 << 30, None) == -1 and "D, H, W >= 2" in _err(clib)
+    bad = list(ok)
+    bad[12] = 0.0
+    assert f(*bad, ws, 1 << 30, None) == -1 and "dz" in _err(clib)
+    bad = list(ok)
+    bad[8] = 5 * 6 * 7 - 1
+    assert f(*bad, ws, 1 << 30, None) == -1 and "member_stride" in _err(clib)
+    assert f(*ok, None, 1 << 30, None) == -1 and "workspace" in _err(clib)
+    assert f(*ok, ws, 64, None) == -1 and "too small" in _err(clib)
+    assert clib.lcp3d_divergence(FAKE, FAKE, FAKE, FAKE, FAKE, None, 4, 4, 4, 1.0, 1.0, 1.0, FAKE, FAKE, None) == -1
+    assert clib.lcp3d_divergence(*([FAKE] * 6), 4, 4, 4, 1.0, 1.0, -1.0, FAKE, FAKE, None) == -1
+    assert clib.lcp3d_map(FAKE, FAKE, 4, 4, 4, iso, 65, FAKE, 0, None, None) == -3
+    assert clib.lcp3d_map(FAKE, FAKE, 4, 4, 4, iso, 2, FAKE, 1, None, None) == -1
