@@ -10,7 +10,10 @@ the GPU library computes for those outputs:
   step in IEEE fp32 (a quantised code: both sides decide it in the kernel's
   precision);
 * ``marching_squares``: the isocontour segments of a scalar field on the grid
-  (reading R18), in FP64.
+  (reading R18), in FP64 except for the two decisions R18 fixes in fp32;
+* ``member_divergence32`` and ``spaghetti_contours``: every member's Eq. 1
+  divergence in fp32 (the operation order of reading R18) and its isocontours,
+  the spaghetti plot of Fig. 1b.
 
 Only ``tests/``, ``__graft_entry__.smoke`` and ``bench.py``'s CPU-baseline leg
 may import this module.  It imports nothing from the GPU library.
@@ -26,13 +29,33 @@ R17 Colour map (the paper names none): a table of stops (t, r, g, b, a) with
     own colour; an optional crossing mask paints the mean-field contour cells
     in a contour colour (the black / cyan contour of Fig. 1a / Fig. 3c at cell
     resolution).
+R18 Isocontour segments (marching squares; the paper shows mean-field
+    isocontours in Fig. 1a / Fig. 3c and spaghetti plots of the members'
+    isocontours in Fig. 1b without defining the extraction).  Cell (i, j) has
+    corners v0 = (i, j), v1 = (i+1, j), v2 = (i+1, j+1), v3 = (i, j+1); a corner
+    is below when f < c (reading R7); edges E0 = v0v1, E1 = v1v2, E2 = v3v2,
+    E3 = v0v3 cross where their corners differ.  A crossing point is
+    interpolated from the edge's lower-coordinate vertex: on a horizontal edge
+    x = i + (c - f(i, j)) / (f(i+1, j) - f(i, j)), on a vertical one
+    y = j + (c - f(i, j)) / (f(i, j+1) - f(i, j)), so neighbouring cells agree
+    on shared points.  Two crossing edges give one segment (lower edge first).
+    The saddles (v0, v2 on one side, v1, v3 on the other) give two: if the
+    centre value ((f0 + f1) + (f2 + f3)) / 4, formed in fp32, lies on v0's side,
+    (E0, E1) and (E2, E3), else (E0, E3) and (E1, E2).  Cells with a NaN corner
+    give none.  Segment (x0, y0, x1, y1) carries the key
+    ((j (W-1) + i) K + k) 2 + s (s = 0, 1 within the cell); for member m of a
+    spaghetti plot the key adds m (H-1)(W-1) K 2.  Lists are in key order.
+    The member divergence of a spaghetti plot is Eq. 1 in fp32 with each
+    operation rounded: (u[i+] - u[i-]) * sx + (v[j+] - v[j-]) * sy with
+    sx = fp32(1 / ((i+ - i-) dx)) (likewise sy), so that the crossing
+    decisions are the kernel's.
 """
 
 from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["colormap_rgba", "pack_rgba"]
+__all__ = ["colormap_rgba", "pack_rgba", "marching_squares", "member_divergence32", "spaghetti_contours"]
 
 _F = np.float32
 
@@ -82,3 +105,90 @@ def colormap_rgba(values, vmin: float, vmax: float, stops, nan_rgba: int = 0, ma
         m = np.asarray(mask, dtype=bool) & ~np.isnan(x)
         out[m] = np.array([(mask_rgba >> (8 * k)) & 0xFF for k in range(4)], dtype=np.uint8)
     return out
+
+
+# --------------------------------------------------------------------------
+# Isocontour segments (reading R18)
+# --------------------------------------------------------------------------
+def _centre32(f0, f1, f2, f3):
+    """The saddle decider's centre value in fp32: ((f0 + f1) + (f2 + f3)) * 0.25."""
+    a = (np.float32(f0) + np.float32(f1)).astype(_F)
+    b = (np.float32(f2) + np.float32(f3)).astype(_F)
+    return ((a + b).astype(_F) * _F(0.25)).astype(_F)
+
+
+def marching_squares(f, isovalues):
+    """Isocontour segments of the scalar field f [H, W] for every isovalue
+    (reading R18).  returns (keys int64 [n], segs float64 [n, 4]) in key order."""
+    f = np.asarray(f, np.float64)
+    h, w = f.shape
+    iso = np.atleast_1d(np.asarray(isovalues, np.float32))
+    kk = iso.size
+    f0, f1 = f[:-1, :-1], f[:-1, 1:]      # v0 = (i, j), v1 = (i+1, j)
+    f3, f2 = f[1:, :-1], f[1:, 1:]        # v3 = (i, j+1), v2 = (i+1, j+1)
+    jj, ii = np.meshgrid(np.arange(h - 1, dtype=np.float64), np.arange(w - 1, dtype=np.float64), indexing="ij")
+    finite = ~(np.isnan(f0) | np.isnan(f1) | np.isnan(f2) | np.isnan(f3))
+    cen = _centre32(f0, f1, f2, f3).astype(np.float64)
+    cell = (np.arange(h - 1)[:, None] * (w - 1) + np.arange(w - 1)[None, :]).astype(np.int64)
+    keys, segs = [], []
+    with np.errstate(invalid="ignore", divide="ignore"):
+        for k in range(kk):
+            c = float(iso[k])
+            b0, b1, b2, b3 = f0 < c, f1 < c, f2 < c, f3 < c
+            # crossing points of the four edges, interpolated from the lower-coordinate vertex
+            p = [np.stack([ii + (c - f0) / (f1 - f0), jj], -1),          # E0: v0 -> v1
+                 np.stack([ii + 1.0, jj + (c - f1) / (f2 - f1)], -1),    # E1: v1 -> v2
+                 np.stack([ii + (c - f3) / (f2 - f3), jj + 1.0], -1),    # E2: v3 -> v2
+                 np.stack([ii, jj + (c - f0) / (f3 - f0)], -1)]          # E3: v0 -> v3
+            cross = [b0 != b1, b1 != b2, b3 != b2, b0 != b3]
+            n_cross = cross[0].astype(int) + cross[1] + cross[2] + cross[3]
+            saddle = finite & (b0 == b2) & (b1 == b3) & (b0 != b1)
+            single = finite & (n_cross == 2)
+            # one segment: the two crossing edges, lower index first
+            for a in range(4):
+                for b in range(a + 1, 4):
+                    sel = single & cross[a] & cross[b]
+                    keys.append(((cell[sel] * kk + k) * 2).ravel())
+                    segs.append(np.concatenate([p[a][sel], p[b][sel]], -1))
+            # saddles: the centre on v0's side joins v0 and v2
+            with_v0 = saddle & ((cen < c) == b0)
+            for sel, pairs in ((with_v0, ((0, 1), (2, 3))), (saddle & ~with_v0, ((0, 3), (1, 2)))):
+                for s_idx, (a, b) in enumerate(pairs):
+                    keys.append(((cell[sel] * kk + k) * 2 + s_idx).ravel())
+                    segs.append(np.concatenate([p[a][sel], p[b][sel]], -1))
+    keys = np.concatenate(keys) if keys else np.zeros(0, np.int64)
+    segs = np.concatenate(segs) if segs else np.zeros((0, 4))
+    order = np.argsort(keys, kind="stable")
+    return keys[order], segs[order].reshape(-1, 4)
+
+
+def member_divergence32(u, v, dx: float, dy: float):
+    """Eq. 1 divergence of every member in IEEE fp32 with the operation order of
+    reading R18.  u, v [M, H, W]; returns float32 [M, H, W]."""
+    u = np.asarray(u, _F)
+    v = np.asarray(v, _F)
+    _, h, w = u.shape
+    i = np.arange(w)
+    il, ih = np.maximum(i - 1, 0), np.minimum(i + 1, w - 1)
+    j = np.arange(h)
+    jl, jh = np.maximum(j - 1, 0), np.minimum(j + 1, h - 1)
+    sx = np.where(ih - il == 2, _F(0.5 / dx), _F(1.0 / dx)).astype(_F)[None, None, :]
+    sy = np.where(jh - jl == 2, _F(0.5 / dy), _F(1.0 / dy)).astype(_F)[None, :, None]
+    gx = ((u[:, :, ih] - u[:, :, il]).astype(_F) * sx).astype(_F)
+    gy = ((v[:, jh, :] - v[:, jl, :]).astype(_F) * sy).astype(_F)
+    return (gx + gy).astype(_F)
+
+
+def spaghetti_contours(u, v, dx: float, dy: float, isovalues):
+    """Isocontours of every member's divergence (Fig. 1b), reading R18.
+    returns (keys int64 [n], segs float64 [n, 4]) in key order."""
+    d = member_divergence32(u, v, dx, dy)
+    m, h, w = d.shape
+    kk = np.atleast_1d(np.asarray(isovalues)).size
+    per = (h - 1) * (w - 1) * kk * 2
+    keys, segs = [], []
+    for mm in range(m):
+        k_m, s_m = marching_squares(d[mm], isovalues)
+        keys.append(k_m + mm * per)
+        segs.append(s_m)
+    return np.concatenate(keys), np.concatenate(segs)
