@@ -49,12 +49,13 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-mc", action="store_true", help="skip the Monte Carlo equal-error comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--workload", choices=["latlon", "batch", "learned", "ocean", "redsea", "colormap", "volume"],
+    ap.add_argument("--workload", choices=["latlon", "batch", "learned", "ocean", "redsea", "colormap", "volume",
+                                           "contours"],
                     default="latlon",
                     help="latlon: the 721x1440 field (default); batch: 256 uneven fields in one persistent launch; "
                          "learned: the non-Gaussian surrogate; ocean: 8192^2 bf16; redsea: the speed-gradient "
                          "preprocessing of the 8192^2 eddy field; colormap: RGBA8 of its LCP map; volume: 3D "
-                         "256^3 fields")
+                         "256^3 fields; contours: spaghetti isocontours of every lat-lon member")
     ap.add_argument("--tile", type=str, default=None,
                     help="batch workload: force the tile shape ROWS,COLS instead of autotuning")
     ap.add_argument("--train-epochs", type=int, default=20, help="learned workload: training epochs (untimed)")
@@ -1137,6 +1138,92 @@ def volume_arm(args):
     return _finish(torch, pg, line, rank)
 
 
+CONTOURS_WORKLOAD = ("contours: spaghetti isocontour segments (marching squares) of every member's divergence, "
+                     "latlon 721x1440, 51 members fp32, 8 isovalues, key-ordered single-pass compaction")
+
+
+def contours_arm(args):
+    """The spaghetti plot of Fig. 1b at scale: every member's divergence
+    isocontours, compacted in key order; the mean-field contours timed beside it."""
+    torch, lib, dev, world, rank, local, pg = gpu_setup()
+    from paper_2510_01190_gb300 import synth
+
+    d = synth.fourier_ensemble(rank, h=H, w=W, m=M, k=K)
+    u, v, iso = torch.from_numpy(d["u"]).to(dev), torch.from_numpy(d["v"]).to(dev), d["isovalues"]
+    seg, key, total = lib.lcp_member_contours(u, v, iso)  # sizes the buffers
+    buf = (torch.empty((total, 4), dtype=torch.float32, device=dev), torch.empty(total, dtype=torch.int64, device=dev))
+
+    # the binding reads the count back after each call; time the kernel alone with
+    # the raw C call on pre-sized buffers so that no host sync sits in the loop
+    clib = lib.load()
+    from paper_2510_01190_gb300 import _binding as B
+
+    nw = clib.lcp_contours_workspace_bytes(M, H, W)
+    ws = torch.empty(nw + 256, dtype=torch.uint8, device=dev)
+    ws_ptr = ws.data_ptr() + (-ws.data_ptr()) % 256
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    iso_t, k, iso_p = B._iso(iso)
+
+    def raw_step():
+        B._check(clib.lcp_member_contours(B._ptr(u), B._ptr(v), 0, M, H, W, H * W, 1.0, 1.0, iso_p, k,
+                                          B._ptr(buf[0]), B._ptr(buf[1]), total, B._ptr(count), B.c_vp(ws_ptr), nw,
+                                          B._stream()))
+
+    total_ms, kern_ms, clocks = timed_steps(torch, raw_step, args.steps, args.warmup, local, pg, dev)
+    assert int(count.item()) == total
+    n = args.steps
+    ms_per_step = total_ms / n
+    member_cells = M * (H - 1) * (W - 1)
+    value = weak_scaling_value(member_cells, world, ms_per_step)
+    alg = 2 * M * H * W * 4 + total * 24
+    peak, peak_kind = measured_hbm_peak()
+    achieved = alg / (kern_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": profiled_traffic("lcp_member_contours_latlon_m51_k8.md", ("contours.cu", "lcp_common.cuh")),
+            "peak_kind": peak_kind, "kernel": "contour_kernel<members fp32> (marching squares + decoupled look-back)",
+            "alg_bytes_per_launch": alg, "kernel_ms": round(kern_ms, 4)}
+    # mean-field contours of the same ensemble, for context
+    mu_d, _ = lib.lcp_divergence(*lib.lcp_stats(u, v))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _, _, mf_total = lib.lcp_contours(mu_d, iso)
+    mf_buf = (torch.empty((mf_total, 4), dtype=torch.float32, device=dev), torch.empty(mf_total, dtype=torch.int64, device=dev))
+    e0.record()
+    for _ in range(20):
+        lib.lcp_contours(mu_d, iso, capacity=mf_total, out=mf_buf)
+    e1.record()
+    torch.cuda.synchronize()
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        from oracle import viz as V
+
+        mm, done, t0 = 0, 0, time.perf_counter()
+        while time.perf_counter() - t0 < 12.0:
+            V.spaghetti_contours(d["u"][mm:mm + 1], d["v"][mm:mm + 1], 1.0, 1.0, iso)
+            done += (H - 1) * (W - 1)
+            mm = (mm + 1) % M
+        dt = time.perf_counter() - t0
+        cpu = {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done // ((H - 1) * (W - 1))} members of {H}x{W}, K={K} (numpy, one thread)",
+               "seconds": round(dt, 2)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": CONTOURS_WORKLOAD, "H": H, "W": W, "M": M, "K": K, "global_batch": world,
+                   "parallelism": f"independent ensembles x{world}" if world > 1 else "single",
+                   "l2": f"no flush: inputs {2 * M * H * W * 4 / 1e9:.2f} GB > 129 MB L2",
+                   "segments_per_step": total, "segments_per_s": total / (ms_per_step / 1e3),
+                   "hbm_frac_of_measured": roof["frac"],
+                   "mean_field": {"segments": mf_total, "ms": round(e0.elapsed_time(e1) / 20, 4),
+                                  "what": "lcp_contours of mu_d (lcp_stats + lcp_divergence untimed), incl. count read-back"}},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": None,
+        "e2e_note": "not measured for this line: the segments stay on the device for drawing",
+        "clocks": clocks, "gpu_launches": n, "gpu": torch.cuda.get_device_name(dev),
+    }
+    return _finish(torch, pg, line, rank)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1153,6 +1240,8 @@ def main():
         return colormap_arm(args)
     if args.workload == "volume":
         return volume_arm(args)
+    if args.workload == "contours":
+        return contours_arm(args)
     return our_arm(args)
 
 

@@ -418,6 +418,8 @@ lcp_status lcp_mc(lcp_mc_mode mode, const float* mu_u, const float* var_u, const
  * (the TMA pipeline's mbarrier waits, the workspace path's waits for
  * statistics rows) gave up; the affected outputs are then undefined.  This
  * call synchronises with the device.
+ * Bit 1: a wait of the learned-surrogate inference (tcgen05 mbarrier) gave up.
+ * Bit 2: a contour look-back wait gave up.
  * Returns LCP_ERR_TIMEOUT if any bit is set, LCP_OK otherwise; `flags` (host,
  * may be NULL) receives the word; `reset` != 0 clears it.
  */
@@ -502,6 +504,47 @@ lcp_status lcp3d_divergence(const float* mu_u, const float* var_u, const float* 
  */
 lcp_status lcp3d_map(const float* mu_d, const float* var_d, int D, int H, int W, const float* iso, int K,
                      void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, lcp_stream_t stream);
+
+/*
+ * Isocontour segments (marching squares).  The paper draws the mean-field
+ * divergence isocontour (Fig. 1a, Fig. 3c) and the spaghetti plot of every
+ * member's isocontour (Fig. 1b).  Cell (i, j) has corners v0 = (i, j),
+ * v1 = (i+1, j), v2 = (i+1, j+1), v3 = (i, j+1); a corner is below when
+ * f < c; edges E0 = v0v1, E1 = v1v2, E2 = v3v2, E3 = v0v3 cross where their
+ * corners differ.  A crossing point is interpolated from the edge's
+ * lower-coordinate vertex in fp32 (x = i + (c - f(i,j)) / (f(i+1,j) - f(i,j))
+ * on a horizontal edge, y likewise on a vertical one), so neighbouring cells
+ * produce the same shared point.  Two crossing edges give one segment (lower
+ * edge first); the saddles (v0, v2 on one side of c, v1, v3 on the other) give
+ * two: if the centre value ((f0 + f1) + (f2 + f3)) * 0.25, each operation an
+ * fp32 operation rounded to nearest, lies on v0's side, (E0, E1) and (E2, E3),
+ * else (E0, E3) and (E1, E2).  Cells with a NaN corner give none.
+ *
+ * Output: seg device fp32 [capacity][4] = (x0, y0, x1, y1) in grid units
+ * (x = column, y = row), 16-byte aligned; key device int64 [capacity] or NULL,
+ * ((j (W-1) + i) K + k) 2 + s (s = 0, 1 within the cell; member m adds
+ * m (H-1)(W-1) K 2).  Segments are written in increasing key order, the same
+ * on every run; count (device uint64) receives the total, of which the first
+ * min(total, capacity) are stored.  The workspace (device, 256-byte aligned,
+ * lcp_contours_workspace_bytes) is cleared by the call; H, W < 2^24.  A look-back wait
+ * that gives up (it should not) sets bit 2 of lcp_device_status.
+ */
+size_t lcp_contours_workspace_bytes(int M, int H, int W);
+
+/* Segments of a scalar field f (device fp32 [H][W], e.g. mu_d of
+ * lcp_divergence) for K <= 64 isovalues (HOST array). */
+lcp_status lcp_contours(const float* field, int H, int W, const float* iso, int K, float* seg, long long* key,
+                        int64_t capacity, unsigned long long* count, void* workspace, size_t workspace_bytes,
+                        lcp_stream_t stream);
+
+/* Segments of every member's Eq. 1 divergence (the spaghetti plot), formed in
+ * fp32 as (u[i+] - u[i-]) * sx + (v[j+] - v[j-]) * sy with sx = fp32(1 / ((i+ - i-) dx))
+ * (likewise sy), each operation rounded to nearest.  Members as for
+ * lcp_stats; K <= 64. */
+lcp_status lcp_member_contours(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
+                               int64_t member_stride, double dx, double dy, const float* iso, int K, float* seg,
+                               long long* key, int64_t capacity, unsigned long long* count, void* workspace,
+                               size_t workspace_bytes, lcp_stream_t stream);
 
 /*
  * lcp_colormap - colour mapping of a scalar map into a headless RGBA8 buffer.

@@ -40,6 +40,9 @@ __all__ = [
     "lcp_philox_fill",
     "lcp_exact_empirical",
     "lcp_colormap",
+    "lcp_contours",
+    "lcp_member_contours",
+    "lcp_contours_workspace_bytes",
     "lcp3d_fused_ws",
     "lcp3d_workspace_bytes",
     "lcp3d_divergence",
@@ -116,6 +119,10 @@ _SIGNATURES = {
     "lcp_batch_autotune": (c_int, [ctypes.POINTER(lcp_batch_plan), c_int, ctypes.POINTER(lcp_tune), c_fp, c_vp]),
     "lcp_exact_empirical": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_double, c_double, c_fp, c_int,
                                     c_vp, c_vp, c_vp]),
+    "lcp_contours_workspace_bytes": (ctypes.c_size_t, [c_int, c_int, c_int]),
+    "lcp_contours": (c_int, [c_vp, c_int, c_int, c_fp, c_int, c_vp, c_vp, c_i64, c_vp, c_vp, ctypes.c_size_t, c_vp]),
+    "lcp_member_contours": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_double, c_double, c_fp, c_int,
+                                    c_vp, c_vp, c_i64, c_vp, c_vp, ctypes.c_size_t, c_vp]),
     "lcp3d_workspace_bytes": (ctypes.c_size_t, [c_int, c_int, c_int, c_int, c_int]),
     "lcp3d_fused_ws": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double,
                                c_double, c_fp, c_int, c_vp, c_int, c_vp, c_vp, ctypes.c_size_t, c_vp]),
@@ -429,6 +436,61 @@ def lcp3d_map(mu_d, var_d, isovalues, out_dtype=torch.float32, mask: bool = Fals
     _check(load().lcp3d_map(_ptr(mu_d), _ptr(var_d), d, h, w, iso_p, k, _ptr(out), _dtype_code(out.dtype),
                             _ptr(mask_out), _stream()))
     return out, mask_out
+
+
+def lcp_contours_workspace_bytes(m: int, h: int, w: int) -> int:
+    return int(load().lcp_contours_workspace_bytes(m, h, w))
+
+
+def _contour_call(launch, m, h, w, k, device, capacity, keys, out):
+    """Run a contour call; with capacity None, estimate, then re-run once if short."""
+    lib = load()
+    need = int(lib.lcp_contours_workspace_bytes(m, h, w))
+    ws, ws_ptr = _workspace(need, device)
+    count = torch.zeros(1, dtype=torch.int64, device=device)
+    cap = capacity if capacity is not None else max(1024, m * (h - 1) * (w - 1) * k // 8)
+    while True:
+        if out is not None and capacity is not None:
+            seg, key = out
+        else:
+            seg = torch.empty((cap, 4), dtype=torch.float32, device=device)
+            key = torch.empty(cap, dtype=torch.int64, device=device) if keys else None
+        _check(launch(_ptr(seg), _ptr(key), cap, _ptr(count), c_vp(ws_ptr), need))
+        total = int(count.item())
+        if capacity is not None or total <= cap:
+            n = min(total, cap)
+            return seg[:n], (key[:n] if key is not None else None), total
+        cap = total
+
+
+def lcp_contours(field, isovalues, capacity=None, keys: bool = True, out=None):
+    """Isocontour segments of a scalar field (float32 CUDA [H, W], e.g. mu_d)
+    in key order: returns (seg [n, 4] float32 (x0, y0, x1, y1), key [n] int64 or
+    None, total).  With ``capacity`` given, at most that many are stored (and
+    ``out`` = (seg, key) may supply the buffers); total is always the full count."""
+    if field.dtype != torch.float32 or not field.is_cuda or field.dim() != 2 or not field.is_contiguous():
+        raise ValueError("field must be a contiguous float32 CUDA tensor [H, W]")
+    h, w = field.shape
+    iso, k, iso_p = _iso(isovalues)
+
+    def launch(seg, key, cap, count, ws, nbytes):
+        return load().lcp_contours(_ptr(field), h, w, iso_p, k, seg, key, cap, count, ws, nbytes, _stream())
+
+    return _contour_call(launch, 1, h, w, k, field.device, capacity, keys, out)
+
+
+def lcp_member_contours(u, v, isovalues, dx: float = 1.0, dy: float = 1.0, capacity=None, keys: bool = True,
+                        out=None):
+    """Spaghetti plot: isocontour segments of every member's divergence (fp32,
+    fixed operation order), in key order.  Returns (seg, key|None, total)."""
+    m, h, w, stride = _members(u, v)
+    iso, k, iso_p = _iso(isovalues)
+
+    def launch(seg, key, cap, count, ws, nbytes):
+        return load().lcp_member_contours(_ptr(u), _ptr(v), _dtype_code(u.dtype), m, h, w, stride, float(dx),
+                                          float(dy), iso_p, k, seg, key, cap, count, ws, nbytes, _stream())
+
+    return _contour_call(launch, m, h, w, k, u.device, capacity, keys, out)
 
 
 class _HostStaging:

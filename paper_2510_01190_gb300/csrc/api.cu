@@ -84,7 +84,8 @@ extern "C" lcp_status lcp_philox_fill(uint64_t seed, uint32_t c1, uint64_t offse
 
 extern "C" lcp_status lcp_device_status(uint32_t* flags, int reset) {
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(LCP_ERR_CUDA, "lcp_device_status: device error");
-    const uint32_t f = read_tma_status(reset != 0) | read_ws_status(reset != 0);
+    const uint32_t f = read_tma_status(reset != 0) | read_ws_status(reset != 0) | (read_sur_status(reset != 0) << 1) |
+                       (read_contour_status(reset != 0) << 2);
     if (flags) *flags = f;
     return f ? fail(LCP_ERR_TIMEOUT, "a bounded device wait gave up (flags 0x%x)", f) : LCP_OK;
 }

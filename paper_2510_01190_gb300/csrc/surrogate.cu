@@ -923,6 +923,17 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
 }
 
 }  // namespace
+
+uint32_t read_sur_status(bool reset) {
+    uint32_t f = 0;
+    cudaMemcpyFromSymbol(&f, g_sur_status, sizeof(f));
+    if (reset) {
+        const uint32_t z = 0;
+        cudaMemcpyToSymbol(g_sur_status, &z, sizeof(z));
+    }
+    return f;
+}
+
 }  // namespace lcp
 
 // ---- host ------------------------------------------------------------------------

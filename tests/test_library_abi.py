@@ -160,3 +160,21 @@ def test_volume_calls_reject_bad_arguments(clib):
     assert clib.lcp3d_divergence(*([FAKE] * 6), 4, 4, 4, 1.0, 1.0, -1.0, FAKE, FAKE, None) == -1
     assert clib.lcp3d_map(FAKE, FAKE, 4, 4, 4, iso, 65, FAKE, 0, None, None) == -3
     assert clib.lcp3d_map(FAKE, FAKE, 4, 4, 4, iso, 2, FAKE, 1, None, None) == -1
+
+
+def test_contour_calls_reject_bad_arguments(clib):
+    iso = (ctypes.c_float * 2)(0.0, 1.0)
+    ws, cnt = ctypes.c_void_p(512), ctypes.c_void_p(1024)
+    f = clib.lcp_contours
+    assert clib.lcp_contours_workspace_bytes(1, 4, 4) == 256 + 8 and clib.lcp_contours_workspace_bytes(1, 1, 4) == 0
+    assert f(None, 4, 4, iso, 2, FAKE, None, 10, cnt, ws, 1 << 20, None) == -1 and "field" in _err(clib)
+    assert f(FAKE, 1, 4, iso, 2, FAKE, None, 10, cnt, ws, 1 << 20, None) == -1
+    assert f(FAKE, 4, 4, iso, 65, FAKE, None, 10, cnt, ws, 1 << 20, None) == -3
+    assert f(FAKE, 4, 4, iso, 2, None, None, 10, cnt, ws, 1 << 20, None) == -1 and "capacity" in _err(clib)
+    assert f(FAKE, 4, 4, iso, 2, ctypes.c_void_p(264), None, 10, cnt, ws, 1 << 20, None) == -1 and "16-byte" in _err(clib)
+    assert f(FAKE, 4, 4, iso, 2, FAKE, None, 10, None, ws, 1 << 20, None) == -1 and "count" in _err(clib)
+    assert f(FAKE, 4, 4, iso, 2, FAKE, None, 10, cnt, None, 1 << 20, None) == -1 and "workspace" in _err(clib)
+    assert f(FAKE, 4, 4, iso, 2, FAKE, None, 10, cnt, ws, 8, None) == -1 and "too small" in _err(clib)
+    g = clib.lcp_member_contours
+    assert g(FAKE, FAKE, 0, 3, 4, 4, 15, 1.0, 1.0, iso, 2, FAKE, None, 10, cnt, ws, 1 << 20, None) == -1
+    assert g(FAKE, FAKE, 0, 3, 4, 4, 16, 1.0, 0.0, iso, 2, FAKE, None, 10, cnt, ws, 1 << 20, None) == -1
