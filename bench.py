@@ -822,8 +822,10 @@ def ocean_arm(args):
     peak, peak_kind = measured_hbm_peak()
     achieved = alg / (kern_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
-            "kernel": "lcp_fused_ws step: stats_ws_kernel<bf16,8> + lcp_rows_kernel<4,nomask,float> per row band",
+            "frac": round(achieved / peak, 4),
+            "traffic": profiled_traffic("lcp_fused_ws_ocean_8192_m20_bf16_k4.md", ("fused_ws.cu", "lcp_common.cuh")),
+            "peak_kind": peak_kind,
+            "kernel": "lcp_fused_ws step: stats_ws_kernel<bf16,4> + lcp_warp_rows_kernel<4,nomask,float> per row band",
             "alg_bytes_per_launch": alg, "kernel_ms": round(kern_ms, 4)}
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
