@@ -1101,8 +1101,8 @@ def volume_arm(args):
     alg = 3 * Mm * Dd * Hh * Ww * 4 + Kk * cells * 4
     peak, peak_kind = measured_hbm_peak()
     achieved = alg / (kern_ms / 1e3) / 1e9
-    ring_planes = max(4, (48 << 20) // (Hh * Ww * 48))
-    slabs = -(-Dd // max(1, min(ring_planes, Dd + 3) - 3))
+    new_planes = min(Dd, max(1, ((96 << 20) // (Hh * Ww * 48) - 3) // 2))  # the ring keeps 2B + 3 planes
+    slabs = -(-Dd // new_planes)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4),
             "traffic": profiled_traffic("lcp3d_fused_ws_256cubed_m20_k4.md", ("volume.cu", "lcp_common.cuh")),

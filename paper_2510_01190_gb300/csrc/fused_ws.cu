@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(kRT, KX <= 4 ? 3 : (KX <= 16 ? 2 : 1))
 constexpr int kWT = 128;  // threads (4 warps = 128 cells) per block
 
 template <int KX, bool MASK, typename OutT, bool IDX32>
-__global__ void __launch_bounds__(kWT, 4)
+__global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer registers, more warps to hide L2
     lcp_warp_rows_kernel(const __grid_constant__ RowsParams p, const __grid_constant__ IsoParams iso) {
     // output and mask element offsets in 32 bits when the outputs fit (IDX32), else 64
     using Off = typename std::conditional<IDX32, uint32_t, int64_t>::type;

@@ -10,7 +10,9 @@
 //    (x0, delta, var, 0) -- member 0, the FP32 mean of the members shifted by
 //    member 0, and the variance -- stored with an L2 evict-last policy into
 //    ring slot (plane % S).  Planes are computed once: the ring keeps the three
-//    older planes the next cells still need.
+//    older planes the next cells still need, and room for the next slab, whose
+//    statistics run on the caller's stream beside this slab's LCP kernel on a
+//    second stream (fork and join by events).
 // 2) lcp3_kernel: a block owns a tile of 31 x 8 cells (32 x 9 vertices, one
 //    thread each) and marches along z over a chunk of cell planes.  Per vertex
 //    plane every thread forms its vertex's divergence Gaussian from six
@@ -40,7 +42,7 @@ constexpr int kL3R = 8;             // cells per LCP tile along y (9 vertex rows
 constexpr int kL3VY = kL3R + 1;
 constexpr int kL3T = 32 * kL3VY;    // LCP threads: one per vertex of the tile
 constexpr int kL3Z = 4;             // cell planes per LCP block (z march)
-constexpr size_t kL2Budget3 = 48ull << 20;
+constexpr size_t kL2Budget3 = 96ull << 20;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 __device__ __forceinline__ uint64_t pol_last() {
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(kS3T, 2) stats3_kernel(const __grid_constant__
 #pragma unroll
             for (int e = 0; e < 4; ++e) s1[c][e] = s2[c][e] = 0.f;
         }
-        constexpr int U = 4;  // members per batch: 12 loads in flight per thread
+        constexpr int U = 2;  // members per batch: 6 loads in flight per thread (registers left for an LCP block)
         int m = 1;
         auto acc = [&](const typename L::raw (&r)[3]) {
 #pragma unroll
@@ -402,15 +404,43 @@ struct Ring {
     size_t bytes;    // 3 * S * hw * 16
 };
 
+// The ring holds S >= 2B + 3 planes, B new planes per slab: the three older planes
+// the next cells need, and room for the next slab's statistics to be written
+// while the LCP of this slab still reads its planes (the two run concurrently).
 Ring ring_for(int D, int H, int W) {
     const size_t plane = (size_t)H * W * 3 * sizeof(float4);
-    int S = (int)std::max<size_t>(4, kL2Budget3 / plane);
-    S = std::min(S, D + 3);
+    const int fit = (int)(kL2Budget3 / plane);
+    int B = std::max(1, (fit - 3) / 2);
+    B = std::min(B, D);
     Ring r;
-    r.S = S;
-    r.B = S - 3;
-    r.bytes = (size_t)S * plane;
+    r.B = B;
+    r.S = 2 * B + 3;
+    r.bytes = (size_t)r.S * plane;
     return r;
+}
+
+// A second stream per host thread and device for the LCP kernels, and ping-pong
+// events for the fork / join with the caller's stream.
+struct SideStream {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev_stats[2] = {nullptr, nullptr}, ev_lcp[2] = {nullptr, nullptr};
+};
+
+lcp_status side_stream(SideStream*& out) {
+    thread_local SideStream per_dev[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fail(LCP_ERR_CUDA, "lcp3d_fused_ws: no device");
+    SideStream& ss = per_dev[dev];
+    if (!ss.st) {
+        if (cudaStreamCreateWithFlags(&ss.st, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(LCP_ERR_CUDA, "lcp3d_fused_ws: stream creation failed");
+        for (int q = 0; q < 2; ++q)
+            if (cudaEventCreateWithFlags(&ss.ev_stats[q], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ss.ev_lcp[q], cudaEventDisableTiming) != cudaSuccess)
+                return fail(LCP_ERR_CUDA, "lcp3d_fused_ws: event creation failed");
+    }
+    out = &ss;
+    return LCP_OK;
 }
 
 template <int KX, bool MASK, typename OutT>
@@ -491,26 +521,47 @@ lcp_status run3(const void* u, const void* v, const void* w, int M, int D, int H
     lp.mask = mask;
     lp.n_words = (W - 1 + 31) / 32;
     lp.kbase = 0;
-    int P = 0, C = 0;
+    // Slab t: statistics of planes [P_t, P_t + B) on the caller's stream, then the LCP of the cells
+    // they complete on the side stream.  The statistics of slab t + 1 overwrite ring slots that only
+    // the LCP of slab t - 1 still reads, so they wait for that one and run beside the LCP of slab t.
+    SideStream* ss = nullptr;
+    lcp_status s = side_stream(ss);
+    if (s != LCP_OK) return s;
+    int P = 0, C = 0, t = 0;
+    bool lcp_pending[2] = {false, false};
     while (C < D - 1) {
         const int Pn = std::min(P + rg.B, D);
+        if (t >= 2 && lcp_pending[t & 1] && cudaStreamWaitEvent(st, ss->ev_lcp[t & 1], 0) != cudaSuccess)
+            return fail(LCP_ERR_CUDA, "lcp3d_fused_ws: stream wait failed");
         sp.n_begin = (int64_t)P * hw;
         sp.n_end = (int64_t)Pn * hw;
         sp.vecload = vec_ok && (sp.n_begin % 4) == 0;
         const int64_t groups = (sp.n_end - sp.n_begin + 3) / 4;
         stats3_kernel<T><<<(unsigned)((groups + kS3T - 1) / kS3T), kS3T, 0, st>>>(sp);
-        lcp_status s = check_launch("lcp3d_fused_ws (statistics)");
+        s = check_launch("lcp3d_fused_ws (statistics)");
         if (s != LCP_OK) return s;
         const int Cn = Pn == D ? D - 1 : std::max(C, Pn - 2);  // cells k need record planes k-1 .. k+2
+        lcp_pending[t & 1] = false;
         if (Cn > C) {
+            if (cudaEventRecord(ss->ev_stats[t & 1], st) != cudaSuccess ||
+                cudaStreamWaitEvent(ss->st, ss->ev_stats[t & 1], 0) != cudaSuccess)
+                return fail(LCP_ERR_CUDA, "lcp3d_fused_ws: fork failed");
             lp.k_begin = C;
             lp.k_end = Cn;
-            s = out_dtype == LCP_F16 ? lcp3_passes<__half>(lp, iso, K, st) : lcp3_passes<float>(lp, iso, K, st);
+            s = out_dtype == LCP_F16 ? lcp3_passes<__half>(lp, iso, K, ss->st) : lcp3_passes<float>(lp, iso, K, ss->st);
             if (s != LCP_OK) return s;
+            if (cudaEventRecord(ss->ev_lcp[t & 1], ss->st) != cudaSuccess)
+                return fail(LCP_ERR_CUDA, "lcp3d_fused_ws: event record failed");
+            lcp_pending[t & 1] = true;
         }
         C = Cn;
         P = Pn;
+        ++t;
     }
+    // join: the caller's stream waits for the last LCP launches
+    for (int q = 0; q < 2; ++q)
+        if (lcp_pending[q] && cudaStreamWaitEvent(st, ss->ev_lcp[q], 0) != cudaSuccess)
+            return fail(LCP_ERR_CUDA, "lcp3d_fused_ws: join failed");
     return LCP_OK;
 }
 
