@@ -121,3 +121,35 @@ def test_mean_field_contours_of_the_divergence(lib):
     assert np.array_equal(gk[keep(gk)], rk[keep(rk)])
     gs = seg.cpu().numpy().astype(np.float64)[keep(gk)]
     assert np.max(np.abs(gs - rs[keep(rk)])) < 1e-2
+
+
+def test_member_contours_latlon_full_sampled(lib):
+    """The bench's workload (721 x 1440, 51 fp32 members, 8 isovalues: ~316 M
+    segments) in one call; the segments of two members inside interior crops
+    against the oracle's spaghetti contours of the crops (cells whose member
+    divergences use no crop-edge stencil)."""
+    d = synth.fourier_ensemble(0)
+    u, v, iso = torch.from_numpy(d["u"]).cuda(), torch.from_numpy(d["v"]).cuda(), d["isovalues"]
+    M_, H_, W_ = u.shape
+    K_ = len(iso)
+    seg, key, total = lib.lcp_member_contours(u, v, iso)
+    assert total > 10 ** 8 and bool(torch.all(key[1:] > key[:-1]))
+    Hc, Wc = H_ - 1, W_ - 1
+    for m, (y0, x0) in ((0, (300, 600)), (37, (10, 1300))):
+        y1, x1 = y0 + 24, x0 + 40
+        ck, cs = V.spaghetti_contours(d["u"][m:m + 1, y0:y1, x0:x1], d["v"][m:m + 1, y0:y1, x0:x1], 1.0, 1.0, iso)
+        # crop cells (il, jl) with 1 <= il <= w-3, 1 <= jl <= h-3 have interior-vertex stencils only
+        wc, hc = x1 - x0 - 1, y1 - y0 - 1
+        cell = ck // 2 // K_
+        jl, il = cell // wc, cell % wc
+        keep = (il >= 1) & (il <= wc - 2) & (jl >= 1) & (jl <= hc - 2)
+        gkey = (((m * Hc + (y0 + jl)) * Wc + (x0 + il)) * K_ + (ck // 2) % K_) * 2 + ck % 2
+        want_k, want_s = gkey[keep], cs[keep] + np.array([x0, y0, x0, y0], np.float64)
+        idx = torch.nonzero(torch.isin(key, torch.from_numpy(want_k).cuda())).flatten()
+        got_k = key[idx].cpu().numpy()
+        assert np.array_equal(got_k, np.sort(want_k))
+        got_s = seg[idx].cpu().numpy().astype(np.float64)
+        order = np.argsort(want_k)
+        assert np.all(np.abs(got_s - want_s[order]) <= _coord_tol(want_s[order]))
+    del u, v, seg, key
+    torch.cuda.empty_cache()

@@ -52,3 +52,17 @@ def test_empirical_mc_converges_to_gpu_exact(lib):
     # binomial standard error at S = 4e4 is at most 2.5e-3; 5 SE over ~5800 cells
     assert np.max(np.abs(e)) <= 5 * 0.0025
     assert np.sqrt(np.mean(e * e)) <= 0.0025
+
+
+def test_exact_empirical_full_size_crop(lib):
+    """The bench's judge call (1024^2, 50 fp32 members, 8 isovalues) against the
+    oracle's exact LCP of a 12 x 12 crop (cells with interior-vertex stencils)."""
+    d = synth.non_gaussian_ensemble(0)
+    u, v = torch.from_numpy(d["u"]).cuda(), torch.from_numpy(d["v"]).cuda()
+    out, _ = lib.lcp_exact_empirical(u, v, d["isovalues"], 1.0, 1.0)
+    y0, x0 = 517, 203
+    ref = O.exact_empirical_lcp(d["u"][:, y0:y0 + 12, x0:x0 + 12], d["v"][:, y0:y0 + 12, x0:x0 + 12], 1.0, 1.0,
+                                d["isovalues"])
+    got = _np(out[:, y0 + 1:y0 + 10, x0 + 1:x0 + 10])
+    assert got.shape == ref.shape
+    assert np.max(np.abs(got - ref)) <= 1e-5

@@ -98,3 +98,25 @@ def test_colormap_overflowing_range(lib):
 def test_colormap_empty(lib):
     x = torch.empty((0, 5, 7), dtype=torch.float32, device="cuda")
     assert lib.lcp_colormap(x).shape == (0, 5, 7, 4)
+
+
+def test_colormap_full_size_sampled(lib):
+    """The bench's map: the 8192^2 eddy field's LCP (4 x 8191^2 fp32) with its
+    mask, in the bench's launch; sampled rows of every plane checked byte for
+    byte against the oracle on the same fp32 values."""
+    if torch.cuda.get_device_properties(0).total_memory < 60e9:
+        pytest.skip("needs the full-size device memory")
+    d = synth.eddy_ensemble_torch(0)
+    lcp, mask = lib.lcp_fused_ws(d["u"], d["v"], d["isovalues"], mask=True)
+    del d
+    torch.cuda.empty_cache()
+    rgba = lib.lcp_colormap(lcp, 0.0, 1.0, mask=mask)
+    K, Hc, Wc = lcp.shape
+    for k in range(K):
+        for r in (0, 1, 4095, Hc - 1):
+            x = lcp[k, r].cpu().numpy()
+            bits = lib.unpack_mask(mask[k:k + 1, r:r + 1], Wc + 1)[0, 0].cpu().numpy()
+            want = V.colormap_rgba(x, 0.0, 1.0, lib.DEFAULT_STOPS, mask=bits, mask_rgba=0xFF000000)
+            assert np.array_equal(rgba[k, r].cpu().numpy(), want), (k, r)
+    del lcp, mask, rgba
+    torch.cuda.empty_cache()
