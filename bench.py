@@ -750,17 +750,14 @@ def learned_arm(args):
     return 0
 
 
-def ws_row_bands(h: int, w: int) -> int:
-    """Row bands of lcp_fused_ws for an h x w grid (one statistics and, for
-    K <= 32, one LCP launch each): bands of record rows that fit a 48 MB
-    budget (two 16-byte records per vertex, 3 halo rows), in multiples of the
-    LCP kernel's 8-row tiles."""
-    rows = (48 << 20) // (2 * w * 16) - 2
-    rows = max(rows, 8)
-    if rows >= h - 1:
-        return 1
-    band = (rows // 8) * 8
-    return -(-(h - 1) // band)
+def ws_row_bands(lib, m: int, h: int, w: int) -> int:
+    """Row bands of lcp_fused_ws (or lcp_speed_gradient_ws) for an h x w grid
+    with lcp_fused_workspace_bytes of workspace, as the library lays them out:
+    one statistics and, for K <= 32, one LCP launch each."""
+    rows = lib.lcp_fused_band_rows(h, w, lib.lcp_fused_workspace_bytes(m, h, w))
+    if rows <= 0:
+        raise RuntimeError(f"lcp_fused_band_rows({h}, {w}) gave {rows}")
+    return -(-(h - 1) // rows)
 
 
 OCEAN_WORKLOAD = ("ocean 8192x8192, 20 members bf16 (5000 Gaussian eddies + noise 0.05), 4 isovalues; "
@@ -854,7 +851,7 @@ def ocean_arm(args):
                        "hbm_frac_of_measured": roof["frac"]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": None,
             "e2e_note": "not measured for this line: 5.4 GB of members per step would be pinned on the host",
-            "clocks": clocks.summary(t_wall0, t_wall1), "gpu_launches": 2 * ws_row_bands(Hh, Ww) * n,
+            "clocks": clocks.summary(t_wall0, t_wall1), "gpu_launches": 2 * ws_row_bands(lib, Mm, Hh, Ww) * n,
             "gpu": torch.cuda.get_device_name(dev),
         }
         print(json.dumps(line), flush=True)
@@ -1005,7 +1002,7 @@ def redsea_arm(args):
                    "lcp_values_per_s": value * Kk, "hbm_frac_of_measured": roof["frac"]},
         "roofline": roof, "unfused": unfused, "cpu_baseline": cpu, "e2e": None,
         "e2e_note": "not measured for this line: 5.4 GB of members per step would be pinned on the host",
-        "clocks": clocks, "gpu_launches": 2 * ws_row_bands(Hh, Ww) * n, "gpu": torch.cuda.get_device_name(dev),
+        "clocks": clocks, "gpu_launches": 2 * ws_row_bands(lib, Mm, Hh, Ww) * n, "gpu": torch.cuda.get_device_name(dev),
     }
     return _finish(torch, pg, line, rank)
 

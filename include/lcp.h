@@ -144,12 +144,24 @@ lcp_status lcp_fused(const void* u, const void* v, lcp_dtype in_dtype, int M, in
  * launched as its programmatic dependent, evaluates Eqs. 2/3 and the LCP of
  * every cell from there, each of its blocks starting as soon as the records it
  * reads are complete (per-band counters in the workspace, reset by the call
- * with a memset node on `stream`).  Grids whose records exceed about 48 MB run
+ * with a memset node on `stream`).  Grids whose records exceed about 96 MB run
  * in bands of rows with one halo row each side, so the workspace stays in L2
- * and its size is bounded.  Calls sharing one workspace must not overlap in
- * time.  workspace == NULL runs lcp_fused.
+ * and its size is bounded.  lcp_fused_workspace_bytes is the size for the
+ * largest bands; a smaller workspace gives smaller bands (at least 8 cell rows
+ * plus the halo, else LCP_ERR_ARG).  Calls sharing one workspace must not
+ * overlap in time.  workspace == NULL runs lcp_fused.
  */
 size_t lcp_fused_workspace_bytes(int M, int H, int W, lcp_dtype in_dtype);
+
+/*
+ * lcp_fused_band_rows - the cell rows per band that lcp_fused_ws (and
+ * lcp_speed_gradient_ws, whose records have the same layout) runs an H x W
+ * grid in with `workspace_bytes` of workspace: H - 1 when the grid runs as
+ * one band, else a multiple of 8; ceil((H - 1) / rows) bands.  Host-only: no
+ * device is touched.  Returns 0 for H < 2 or W < 2, or a workspace smaller
+ * than the smallest band needs.
+ */
+int lcp_fused_band_rows(int H, int W, size_t workspace_bytes);
 
 lcp_status lcp_fused_ws(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
                         int64_t member_stride, int ddof, double dx, double dy, const float* iso, int K,
@@ -169,9 +181,11 @@ lcp_status lcp_fused_ws(const void* u, const void* v, lcp_dtype in_dtype, int M,
  * The per-band counters that must start at zero are cleared on `stream` by
  * every call.  The one array is shared by all calls on a device: calls that
  * overlap in time (other streams, other host threads) race and give undefined
- * results.  Errors: LCP_ERR_ARG when lcp_fused_workspace_bytes(M, H, W,
- * in_dtype) exceeds 64 MiB (grids wider than about 190,000 vertices) or on any
- * argument lcp_fused_ws rejects; LCP_ERR_CUDA when the address lookup fails.
+ * results.  The row bands shrink to fit the 64 MiB (wide grids run in more,
+ * smaller bands than with lcp_fused_workspace_bytes of workspace).  Errors:
+ * LCP_ERR_ARG when even the smallest band (8 cell rows plus the halo) needs more
+ * than 64 MiB (grids wider than about 190,000 vertices) or on any argument
+ * lcp_fused_ws rejects; LCP_ERR_CUDA when the address lookup fails.
  */
 lcp_status lcp_fused_static_ws(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
                                int64_t member_stride, int ddof, double dx, double dy, const float* iso, int K,

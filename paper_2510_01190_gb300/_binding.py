@@ -26,6 +26,7 @@ __all__ = [
     "lcp_fused_ws",
     "lcp_fused_static_ws",
     "lcp_fused_workspace_bytes",
+    "lcp_fused_band_rows",
     "lcp_fused_host",
     "lcp_field_desc",
     "lcp_tune",
@@ -110,6 +111,7 @@ _SIGNATURES = {
     "lcp_philox_fill": (c_int, [c_u64, c_u32, c_u64, c_i64, c_vp, c_vp]),
     "lcp_device_status": (c_int, [ctypes.POINTER(c_u32), c_int]),
     "lcp_fused_workspace_bytes": (ctypes.c_size_t, [c_int, c_int, c_int, c_int]),
+    "lcp_fused_band_rows": (c_int, [c_int, c_int, ctypes.c_size_t]),
     "lcp_fused_ws": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double, c_fp, c_int,
                              c_vp, c_int, c_vp, c_vp, ctypes.c_size_t, c_vp]),
     "lcp_batch_workspace_bytes": (ctypes.c_size_t, [c_int, c_int]),
@@ -285,6 +287,13 @@ def lcp_fused_workspace_bytes(m: int, h: int, w: int, dtype=torch.float32) -> in
     return int(load().lcp_fused_workspace_bytes(m, h, w, _dtype_code(dtype)))
 
 
+def lcp_fused_band_rows(h: int, w: int, workspace_bytes: int) -> int:
+    """Cell rows per band of ``lcp_fused_ws`` for an h x w grid and that many
+    workspace bytes (h - 1: one band); 0 when the workspace is too small.
+    Host arithmetic only."""
+    return int(load().lcp_fused_band_rows(h, w, workspace_bytes))
+
+
 _WS = {}
 
 
@@ -301,8 +310,9 @@ def _workspace(nbytes: int, device):
 def lcp_fused_ws(u, v, isovalues, dx: float = 1.0, dy: float = 1.0, ddof: int = 1, out_dtype=torch.float32,
                  mask: bool = False, out=None, mask_out=None, workspace=None):
     """``lcp_fused`` through the persistent dataflow kernel, with a device
-    workspace (a uint8 CUDA tensor of at least ``lcp_fused_workspace_bytes``;
-    by default one cached per device and stream).  Returns (lcp, mask_words|None)."""
+    workspace (a uint8 CUDA tensor, 256-byte aligned, ideally of
+    ``lcp_fused_workspace_bytes``: a smaller one runs smaller row bands; by
+    default one cached per device and stream).  Returns (lcp, mask_words|None)."""
     m, h, w, stride = _members(u, v)
     iso, k, iso_p = _iso(isovalues)
     out, mask_out = _outputs(k, h, w, u.device, out_dtype, mask, out, mask_out)

@@ -31,9 +31,12 @@
 // backoff -- only for the statistics rows of its own band.  The wait cannot
 // deadlock: every block it waits for is already running.
 //
-// Grids whose records would not fit comfortably in L2 are processed in bands
-// of rows (records of the band plus one halo row on each side, then its
-// cells), so the workspace never spills to HBM.
+// Grids whose records would not fit comfortably in L2 (a 96 MB budget) are
+// processed in bands of rows (records of the band plus one halo row on each
+// side, then its cells), so the workspace never spills to HBM; a smaller
+// workspace than lcp_fused_workspace_bytes reports gives smaller bands.
+#include <algorithm>
+#include <cstdint>
 #include <cstdlib>
 #include <mutex>
 #include <type_traits>
@@ -50,7 +53,7 @@ constexpr int kST = 256;           // stats kernel threads
 constexpr int kRT = 256;           // LCP kernel threads = cell columns per tile
 constexpr int kTR = 8;             // cell rows per LCP tile
 constexpr int kMaxKPass = 32;      // isovalues per LCP launch
-constexpr size_t kL2Budget = 48ull << 20;  // workspace bytes a band may occupy
+constexpr size_t kL2Budget = 96ull << 20;  // workspace bytes a band may occupy (of the 129 MB L2)
 constexpr long long kWaitBudget = 4000000000ll;  // clock cycles (~2 s) before a dependency wait gives up
 
 // Statistics blocks [blo, bhi] of the statistics grid that cover the rows LCP
@@ -650,22 +653,32 @@ struct Layout {
     size_t total;
 };
 
-Layout layout(int H, int W) {
-    Layout L;
+// Bands of record rows that fit both the L2 budget and `cap` bytes of workspace
+// (the caller's); at least one LCP tile of kTR rows plus the halo.
+Layout layout(int H, int W, size_t cap = SIZE_MAX) {
     const size_t row_bytes = (size_t)2 * W * sizeof(float4);
+    auto fill = [&](Layout& L, long rows) {
+        if (rows >= H - 1) {
+            L.band_rows = H - 1;
+            L.ws_rows = H;
+        } else {
+            L.band_rows = (int)(rows / kTR) * kTR;
+            L.ws_rows = L.band_rows + 3;
+        }
+        L.nby = (L.band_rows + kTR - 1) / kTR;
+        L.ctr_bytes = ((size_t)L.nby * 4 + 255) & ~(size_t)255;
+        L.plane_bytes = ((size_t)L.ws_rows * W * sizeof(float4) + 255) & ~(size_t)255;
+        L.total = L.ctr_bytes + 2 * L.plane_bytes;
+    };
     long rows = (long)(kL2Budget / row_bytes) - 2;
     if (rows < kTR) rows = kTR;
-    if (rows >= H - 1) {
-        L.band_rows = H - 1;
-        L.ws_rows = H;
-    } else {
-        L.band_rows = (int)(rows / kTR) * kTR;
-        L.ws_rows = L.band_rows + 3;
+    Layout L;
+    fill(L, rows);  // the budget's layout: a workspace of exactly L.total keeps it
+    if (L.total > cap) {
+        // a smaller workspace: the largest band whose rows plus 3 halo/record rows fit it
+        fill(L, std::max<long>((long)(cap / row_bytes) - 3, kTR));
+        while (L.total > cap && L.band_rows > kTR) fill(L, L.band_rows - kTR);
     }
-    L.nby = (L.band_rows + kTR - 1) / kTR;
-    L.ctr_bytes = ((size_t)L.nby * 4 + 255) & ~(size_t)255;
-    L.plane_bytes = ((size_t)L.ws_rows * W * sizeof(float4) + 255) & ~(size_t)255;
-    L.total = L.ctr_bytes + 2 * L.plane_bytes;
     return L;
 }
 
@@ -786,9 +799,9 @@ lcp_status launch_rows(const RowsParams& p0, const float* iso, int K, cudaStream
 
 template <typename T, int VEC>
 lcp_status run(const void* u, const void* v, int M, int H, int W, int64_t stride, int ddof, double dx, double dy,
-               const float* iso, int K, void* out, lcp_dtype out_dtype, uint32_t* mask, void* ws, bool vecload,
-               cudaStream_t st) {
-    const Layout L = layout(H, W);
+               const float* iso, int K, void* out, lcp_dtype out_dtype, uint32_t* mask, void* ws, size_t ws_bytes,
+               bool vecload, cudaStream_t st) {
+    const Layout L = layout(H, W, ws_bytes);
     const int Hc = H - 1;
     uint32_t* dep = reinterpret_cast<uint32_t*>(ws);
     float4* rec = reinterpret_cast<float4*>(reinterpret_cast<char*>(ws) + L.ctr_bytes);
@@ -846,8 +859,8 @@ lcp_status run(const void* u, const void* v, int M, int H, int W, int64_t stride
 
 }  // namespace
 
-WsGeometry ws_geometry(int H, int W) {
-    const Layout L = layout(H, W);
+WsGeometry ws_geometry(int H, int W, size_t cap) {
+    const Layout L = layout(H, W, cap);
     WsGeometry g;
     g.band_rows = L.band_rows;
     g.ctr_bytes = L.ctr_bytes;
@@ -897,6 +910,12 @@ extern "C" size_t lcp_fused_workspace_bytes(int M, int H, int W, lcp_dtype in_dt
     return layout(H, W).total;
 }
 
+extern "C" int lcp_fused_band_rows(int H, int W, size_t workspace_bytes) {
+    if (H < 2 || W < 2) return 0;
+    const Layout L = layout(H, W, workspace_bytes);
+    return L.total <= workspace_bytes ? L.band_rows : 0;
+}
+
 extern "C" lcp_status lcp_fused_ws(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
                                    int64_t member_stride, int ddof, double dx, double dy, const float* iso, int K,
                                    void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, void* workspace,
@@ -912,17 +931,18 @@ extern "C" lcp_status lcp_fused_ws(const void* u, const void* v, lcp_dtype in_dt
     if (out_dtype != LCP_F32 && out_dtype != LCP_F16) return fail(LCP_ERR_ARG, "lcp_fused_ws: out dtype must be F32 or F16");
     if ((uintptr_t)mask & 3) return fail(LCP_ERR_ARG, "lcp_fused_ws: mask must be 4-byte aligned");
     if ((uintptr_t)workspace & 255) return fail(LCP_ERR_ARG, "lcp_fused_ws: workspace must be 256-byte aligned");
-    const Layout L = layout(H, W);
+    const Layout L = layout(H, W, workspace_bytes);
     if (workspace_bytes < L.total)
-        return fail(LCP_ERR_ARG, "lcp_fused_ws: workspace too small (%zu < %zu bytes)", workspace_bytes, L.total);
+        return fail(LCP_ERR_ARG, "lcp_fused_ws: workspace too small (%zu < %zu bytes for the smallest band)",
+                    workspace_bytes, L.total);
     if ((H - 1 + kTR - 1) / kTR > 65535) return fail(LCP_ERR_UNSUPPORTED, "lcp_fused_ws: H too large");
     const int64_t stride = M > 1 ? member_stride : (int64_t)H * W;
     cudaStream_t st = (cudaStream_t)stream;
     const bool in16 = aligned16(u) && aligned16(v);
     if (in_dtype == LCP_F32)
         return run<float, 4>(u, v, M, H, W, stride, ddof, dx, dy, iso, K, lcp_out, out_dtype, mask, workspace,
-                             in16 && stride % 4 == 0, st);
+                             workspace_bytes, in16 && stride % 4 == 0, st);
     const bool in8 = ((uintptr_t)u & 7) == 0 && ((uintptr_t)v & 7) == 0;
     return run<__nv_bfloat16, 4>(u, v, M, H, W, stride, ddof, dx, dy, iso, K, lcp_out, out_dtype, mask, workspace,
-                                 in8 && stride % 4 == 0, st);
+                                 workspace_bytes, in8 && stride % 4 == 0, st);
 }

@@ -52,12 +52,8 @@ extern "C" lcp_status lcp_fused_static_ws(const void* u, const void* v, lcp_dtyp
                                           lcp_stream_t stream) {
     if (H < 2 || W < 2 || M < 1)
         return lcp::fail(LCP_ERR_ARG, "lcp_fused_static_ws: need M >= 1, H >= 2, W >= 2 (got %d, %d, %d)", M, H, W);
-    const size_t need = lcp_fused_workspace_bytes(M, H, W, in_dtype);
-    if (need == 0 || need > kStaticWsBytes)
-        return lcp::fail(LCP_ERR_ARG,
-                         "lcp_fused_static_ws: a %d x %d grid needs %zu bytes of scratch, more than the %zu-byte "
-                         "static maximum; use lcp_fused_ws with a caller workspace",
-                         H, W, need, kStaticWsBytes);
+    // the row bands shrink to fit the static scratch; lcp_fused_ws rejects grids whose
+    // smallest band does not fit
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();

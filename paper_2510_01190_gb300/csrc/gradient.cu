@@ -315,11 +315,11 @@ __global__ void __launch_bounds__(256) grad_members_kernel(const T* __restrict__
 template <typename T>
 lcp_status run_grad(const void* u, const void* v, int M, int H, int W, int64_t stride, int ddof, double dx, double dy,
                     const float* iso, int K, void* out, lcp_dtype out_dtype, uint32_t* mask, void* ws,
-                    cudaStream_t st) {
+                    size_t ws_bytes, cudaStream_t st) {
     // paired loads need every row and member to start on an even column
     const bool paired = W % 2 == 0 && stride % 2 == 0 && ((uintptr_t)u % (2 * sizeof(T))) == 0 &&
                         ((uintptr_t)v % (2 * sizeof(T))) == 0;
-    const WsGeometry G = ws_geometry(H, W);
+    const WsGeometry G = ws_geometry(H, W, ws_bytes);
     float4* rec = reinterpret_cast<float4*>(reinterpret_cast<char*>(ws) + G.ctr_bytes);
     const int64_t ps = (int64_t)(G.plane_bytes / sizeof(float4));
     const int Hc = H - 1;
@@ -399,14 +399,16 @@ extern "C" lcp_status lcp_speed_gradient_ws(const void* u, const void* v, lcp_dt
     if ((uintptr_t)mask & 3) return fail(LCP_ERR_ARG, "%s: mask must be 4-byte aligned", fn);
     if (!workspace || ((uintptr_t)workspace & 255)) return fail(LCP_ERR_ARG, "%s: need a 256-byte aligned workspace", fn);
     if ((int64_t)H * W >= (1ll << 31)) return fail(LCP_ERR_UNSUPPORTED, "%s: H * W must be below 2^31", fn);
-    const WsGeometry G = ws_geometry(H, W);
+    const WsGeometry G = ws_geometry(H, W, workspace_bytes);
     if (workspace_bytes < G.total)
-        return fail(LCP_ERR_ARG, "%s: workspace too small (%zu < %zu bytes)", fn, workspace_bytes, G.total);
+        return fail(LCP_ERR_ARG, "%s: workspace too small (%zu < %zu bytes for the smallest band)", fn, workspace_bytes,
+                    G.total);
     if ((H + 2 + kPR - 1) / kPR > 65535) return fail(LCP_ERR_UNSUPPORTED, "%s: H too large", fn);
     const int64_t stride = M > 1 ? member_stride : (int64_t)H * W;
     cudaStream_t st = (cudaStream_t)stream;
     if (in_dtype == LCP_F32)
-        return run_grad<float>(u, v, M, H, W, stride, ddof, dx, dy, iso, K, lcp_out, out_dtype, mask, workspace, st);
+        return run_grad<float>(u, v, M, H, W, stride, ddof, dx, dy, iso, K, lcp_out, out_dtype, mask, workspace,
+                               workspace_bytes, st);
     return run_grad<__nv_bfloat16>(u, v, M, H, W, stride, ddof, dx, dy, iso, K, lcp_out, out_dtype, mask, workspace,
-                                   st);
+                                   workspace_bytes, st);
 }

@@ -52,7 +52,8 @@ uint32_t read_ws_status(bool reset);   // workspace path (LCP blocks waiting on 
 uint32_t read_contour_status(bool reset);  // contour compaction (decoupled look-back waits)
 uint32_t read_sur_status(bool reset);      // learned-surrogate inference (tcgen05 mbarrier waits)
 
-// Workspace of lcp_fused_ws: bands of `band_rows` cell rows; a counter header of
+// Workspace of lcp_fused_ws: bands of `band_rows` cell rows (within a 96 MB L2
+// budget and the workspace given, at least 8 rows); a counter header of
 // ctr_bytes, then two record planes (u, v) of plane_bytes each.  A record is
 // float4 (x0, delta, var, 0) per vertex and component: member 0, the FP32 mean
 // of the members shifted by member 0, and the variance.
@@ -60,7 +61,7 @@ struct WsGeometry {
     int band_rows;
     size_t ctr_bytes, plane_bytes, total;
 };
-WsGeometry ws_geometry(int H, int W);
+WsGeometry ws_geometry(int H, int W, size_t cap);  // bands that fit `cap` bytes of workspace
 // Eqs. 2/3 and the LCP of cell rows [r0, r1) (plus the mask) from such record
 // planes, whose row 0 is grid row row0 and which hold rows max(r0-1, 0) ..
 // min(r1+1, H-1); launched in stream order after the kernel that wrote them.

@@ -88,8 +88,8 @@ def test_speed_gradient_ws_many_isovalues(lib, k, out_dtype):
 
 
 def test_speed_gradient_ws_several_bands(lib):
-    """8192 columns: the 48 MB record budget holds 184 cell rows, so 400 rows
-    run as three bands whose halo rows must join seamlessly."""
+    """8192 columns: the 96 MB record budget holds 376 cell rows, so 400 rows
+    run as two bands whose halo rows must join seamlessly."""
     u, v = _members(12, 3, 400, 8192, torch.float32, scale=0.5)
     _check_lcp(lib, u, v, [-0.2, 0.1], 1.0, 1.0)
 

@@ -320,12 +320,21 @@ def test_device_status_clear_after_runs(lib):
     assert lib.lcp_device_status() == 0
 
 
-def test_fused_ws_rejects_small_workspace(lib):
-    d = _fields(20, 64, 4, seed=15, k=2)
-    need = lib.lcp_fused_workspace_bytes(4, 20, 64)
-    ws = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+def test_fused_ws_small_workspace_runs_smaller_bands(lib):
+    """A workspace below lcp_fused_workspace_bytes runs the grid in smaller row
+    bands with identical results; one below the smallest band is rejected."""
+    d = _fields(60, 64, 4, seed=15, k=2)
+    u, v = _dev(d["u"]), _dev(d["v"])
+    need = lib.lcp_fused_workspace_bytes(4, 60, 64)
+    ref, ref_mask = lib.lcp_fused_ws(u, v, d["isovalues"], mask=True)
+    ws = torch.empty(need // 2 + 512, dtype=torch.uint8, device="cuda")
+    base = ws.data_ptr() % 256
+    ws = ws[(256 - base) % 256:]
+    got, got_mask = lib.lcp_fused_ws(u, v, d["isovalues"], mask=True, workspace=ws)
+    assert torch.equal(got, ref) and torch.equal(got_mask, ref_mask)
+    tiny = torch.empty(1024, dtype=torch.uint8, device="cuda")
     with pytest.raises(lib.LcpError) as e:
-        lib.lcp_fused_ws(_dev(d["u"]), _dev(d["v"]), d["isovalues"], workspace=ws)
+        lib.lcp_fused_ws(u, v, d["isovalues"], workspace=tiny)
     assert e.value.status == -1
 
 

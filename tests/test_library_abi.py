@@ -178,3 +178,31 @@ def test_contour_calls_reject_bad_arguments(clib):
     g = clib.lcp_member_contours
     assert g(FAKE, FAKE, 0, 3, 4, 4, 15, 1.0, 1.0, iso, 2, FAKE, None, 10, cnt, ws, 1 << 20, None) == -1
     assert g(FAKE, FAKE, 0, 3, 4, 4, 16, 1.0, 0.0, iso, 2, FAKE, None, 10, cnt, ws, 1 << 20, None) == -1
+
+
+def test_fused_band_rows_keep_one_band_when_the_workspace_is_exact(clib):
+    """lcp_fused_band_rows is host arithmetic: a workspace of exactly
+    lcp_fused_workspace_bytes keeps the budget's bands (one band whenever the
+    grid fits the 96 MB budget), a smaller one gives smaller bands in whole
+    8-row tiles, and one below the smallest band gives 0."""
+    rows = clib.lcp_fused_band_rows
+    need = clib.lcp_fused_workspace_bytes
+    for h, w in ((721, 1440), (2, 2), (9, 2), (60, 64), (601, 4096), (2185, 2), (3000, 1)):
+        if w < 2:
+            assert rows(h, w, 1 << 30) == 0
+            continue
+        assert rows(h, w, need(1, h, w, 0)) == h - 1, (h, w)
+        assert rows(h, w, need(1, h, w, 0) + 12345) == h - 1
+    assert rows(1001, 4096, need(1, 1001, 4096, 0)) == 760  # 131 MB of records: 766 rows in 96 MB
+    # 8192 columns: 512 KiB of records per row, 382 rows in 96 MB -> bands of 376
+    full = need(20, 8192, 8192, 1)
+    assert rows(8192, 8192, full) == 376
+    last = 376
+    for cap in (full - 1, 80 << 20, 64 << 20, 20 << 20, 6 << 20):
+        r = rows(8192, 8192, cap)
+        assert 8 <= r < 376 and r % 8 == 0 and r <= last, (cap, r)
+        assert (r + 3) * 8192 * 32 <= cap < (r + 8 + 3) * 8192 * 32 + 4096, (cap, r)
+        last = r
+    assert rows(8192, 8192, 64 << 20) == 248  # the static 64 MiB scratch of lcp_fused_static_ws
+    assert rows(8192, 8192, 11 * 8192 * 32 - 1) == 0  # below 8 rows plus 3 halo/record rows
+    assert rows(1, 8192, full) == 0 and rows(8192, 8192, 0) == 0

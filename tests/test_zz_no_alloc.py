@@ -17,6 +17,8 @@ CASES = [
     (97, 203, 9, 5, torch.float32),
     (64, 130, 12, 3, torch.bfloat16),
     (721, 1440, 51, 8, torch.float32),
+    # 600 x 8192: one band would need ~95 MB; the 64 MiB scratch runs smaller bands
+    (600, 8192, 3, 2, torch.float32),
 ]
 
 
@@ -55,8 +57,10 @@ def test_static_scratch_matches_workspace_path_twice(lib, h, w, m, k, dt):
 def test_static_scratch_rejects_grids_above_its_maximum(lib):
     clib = lib.load()
     iso_c = (ctypes.c_float * 1)(0.0)
-    # 100 x 400000 needs about 140 MB of scratch, more than the 64 MiB array
-    s = clib.lcp_fused_static_ws(None, None, 0, 2, 100, 400000, 100 * 400000, 1, 1.0, 1.0, iso_c, 1, None, 0, None,
+    # 100 x 400000: even the smallest band (8 cell rows + halo) needs about 140 MB
+    # of scratch, more than the 64 MiB array (stand-in pointers: nothing is read)
+    fake = ctypes.c_void_p(256)
+    s = clib.lcp_fused_static_ws(fake, fake, 0, 2, 100, 400000, 100 * 400000, 1, 1.0, 1.0, iso_c, 1, fake, 0, None,
                                  None)
     assert s == -1
-    assert b"static maximum" in clib.lcp_last_error()
+    assert b"smallest band" in clib.lcp_last_error()
