@@ -338,6 +338,28 @@ def test_fused_ws_small_workspace_runs_smaller_bands(lib):
     assert e.value.status == -1
 
 
+def test_fused_ws_bands_finish_on_the_callers_stream(lib):
+    """A grid run in several bands on a caller's (non-default) stream: a copy
+    queued right after the call on that stream, with no device synchronisation
+    in between, sees the finished map of every band."""
+    d = _fields(60, 64, 4, seed=17, k=3)
+    u, v = _dev(d["u"]), _dev(d["v"])
+    ref, ref_mask = lib.lcp_fused_ws(u, v, d["isovalues"], mask=True)
+    need = lib.lcp_fused_workspace_bytes(4, 60, 64)
+    ws = torch.empty(need // 2 + 512, dtype=torch.uint8, device="cuda")
+    ws = ws[(256 - ws.data_ptr() % 256) % 256:]
+    assert 8 <= lib.lcp_fused_band_rows(60, 64, ws.numel()) < 59
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            out = torch.full_like(ref, float("nan"))
+            mask = torch.full_like(ref_mask, -1)
+            lib.lcp_fused_ws(u, v, d["isovalues"], mask=True, out=out, mask_out=mask, workspace=ws)
+            seen, seen_mask = out.clone(), mask.clone()
+            assert torch.equal(seen, ref) and torch.equal(seen_mask, ref_mask)
+
+
 def test_fused_ws_repeated_calls_reuse_workspace(lib):
     """Counters are reset by every call: back-to-back calls on one workspace agree."""
     d = _fields(50, 300, 9, seed=16, k=3)

@@ -17,7 +17,7 @@ CASES = [
     (97, 203, 9, 5, torch.float32),
     (64, 130, 12, 3, torch.bfloat16),
     (721, 1440, 51, 8, torch.float32),
-    # 600 x 8192: one band would need ~95 MB; the 64 MiB scratch runs smaller bands
+    # 600 x 8192: 157 MB of records; the 64 MiB scratch runs 248-row bands
     (600, 8192, 3, 2, torch.float32),
 ]
 
