@@ -370,7 +370,9 @@ def our_arm(args):
         torch.cuda.synchronize()
         e_ms = e0.elapsed_time(e1) / args.e2e_steps
         e2e = {"value": world * Hc * Wc / (e_ms / 1e3), "unit": UNIT, "ms_per_step": round(e_ms, 4),
-               "h2d_bytes_per_step": 2 * M * H * W * 4, "d2h_bytes_per_step": K * Hc * Wc * 4 + K * Hc * n_words * 4}
+               "h2d_bytes_per_step": 2 * M * H * W * 4, "d2h_bytes_per_step": K * Hc * Wc * 4 + K * Hc * n_words * 4,
+               "h2d_mode": "pinned members read in place by the statistics kernel over the CPU-GPU link",
+               "api": "lcp_fused_host (pinned host members in, pinned LCP map and mask words out)"}
 
     vs_mc = None
     if not args.no_mc and rank == 0:

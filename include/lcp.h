@@ -149,7 +149,11 @@ lcp_status lcp_fused(const void* u, const void* v, lcp_dtype in_dtype, int M, in
  * and its size is bounded.  lcp_fused_workspace_bytes is the size for the
  * largest bands; a smaller workspace gives smaller bands (at least 8 cell rows
  * plus the halo, else LCP_ERR_ARG).  Calls sharing one workspace must not
- * overlap in time.  workspace == NULL runs lcp_fused.
+ * overlap in time.  workspace == NULL runs lcp_fused.  With a workspace, u and
+ * v may also be pinned host memory that the device can address (cudaHostAlloc
+ * under unified addressing): the statistics kernel then reads each member byte
+ * once over the CPU-GPU link, with no staging copy; the host planes must stay
+ * unchanged until the work on `stream` is complete.
  */
 size_t lcp_fused_workspace_bytes(int M, int H, int W, lcp_dtype in_dtype);
 

@@ -516,26 +516,48 @@ _STAGING = _HostStaging()
 
 def lcp_fused_host(u_host, v_host, isovalues, dx: float = 1.0, dy: float = 1.0, ddof: int = 1,
                    out_host=None, mask_host=None, device="cuda"):
-    """End-to-end call for host-resident ensembles: copy the members (pinned
-    host tensors [M, H, W]) to the device, run ``lcp_fused`` and copy the LCP
-    map (and mask words, if ``mask_host`` is given) back into the pinned host
-    outputs, all on the current stream.  Returns (out_host, mask_host); the
-    copies are complete once the stream is synchronised."""
+    """End-to-end call for host-resident ensembles [M, H, W] (fp32 or bf16).
+    Pinned members are read in place by the statistics kernel of
+    ``lcp_fused_ws`` over the CPU-GPU link, each byte once, with no staging
+    copy; pageable ones are first copied into a device staging buffer.  The
+    LCP map (and the mask words, if ``mask_host`` is given) is copied back into
+    the host outputs (pinned ones asynchronously), all on the current stream.
+    Returns (out_host, mask_host); the results are complete, and the members
+    may be changed again, once the stream is synchronised."""
     if u_host.is_cuda or v_host.is_cuda:
         raise ValueError("lcp_fused_host takes host tensors")
+    if u_host.dim() != 3 or u_host.shape != v_host.shape or u_host.dtype != v_host.dtype:
+        raise ValueError("u and v must be [M, H, W] host tensors of one shape and dtype")
+    if not (u_host.is_contiguous() and v_host.is_contiguous()):
+        raise ValueError("host members must be contiguous [M][H][W]")
     m, h, w = u_host.shape
-    iso, k, _ = _iso(isovalues)
-    key = (tuple(u_host.shape), u_host.dtype, k, mask_host is not None, str(device))
+    iso, k, iso_p = _iso(isovalues)
+    dev = torch.device(device)
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    in_place = u_host.is_pinned() and v_host.is_pinned()
+    key = (tuple(u_host.shape), u_host.dtype, k, mask_host is not None, str(dev), in_place)
     if _STAGING.key != key:
-        _STAGING.bufs = (torch.empty_like(u_host, device=device), torch.empty_like(v_host, device=device),
-                         torch.empty((k, h - 1, w - 1), dtype=torch.float32, device=device),
-                         torch.empty((k, h - 1, mask_words_per_row(w)), dtype=torch.int32, device=device)
+        _STAGING.bufs = (None if in_place else torch.empty_like(u_host, device=dev),
+                         None if in_place else torch.empty_like(v_host, device=dev),
+                         torch.empty((k, h - 1, w - 1), dtype=torch.float32, device=dev),
+                         torch.empty((k, h - 1, mask_words_per_row(w)), dtype=torch.int32, device=dev)
                          if mask_host is not None else None)
         _STAGING.key = key
     ud, vd, od, md = _STAGING.bufs
-    ud.copy_(u_host, non_blocking=True)
-    vd.copy_(v_host, non_blocking=True)
-    lcp_fused_ws(ud, vd, iso, dx, dy, ddof, mask=md is not None, out=od, mask_out=md)
+    if in_place:
+        lib = load()
+        code = _dtype_code(u_host.dtype)
+        need = int(lib.lcp_fused_workspace_bytes(m, h, w, code))
+        with torch.cuda.device(dev):
+            _, ws_ptr = _workspace(need, dev)
+            _check(lib.lcp_fused_ws(c_vp(u_host.data_ptr()), c_vp(v_host.data_ptr()), code, m, h, w, h * w, ddof,
+                                    float(dx), float(dy), iso_p, k, _ptr(od), LCP_F32, _ptr(md), c_vp(ws_ptr), need,
+                                    _stream()))
+    else:
+        ud.copy_(u_host, non_blocking=True)
+        vd.copy_(v_host, non_blocking=True)
+        lcp_fused_ws(ud, vd, iso, dx, dy, ddof, mask=md is not None, out=od, mask_out=md)
     if out_host is None:
         out_host = torch.empty(od.shape, dtype=od.dtype, pin_memory=True)
     out_host.copy_(od, non_blocking=True)

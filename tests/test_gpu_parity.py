@@ -435,3 +435,28 @@ def test_fused_ws_ocean_8192_bf16_sampled(lib):
         assert np.array_equal(gm[guard], ref["mask"][guard])
     del u, v, lcp, mask, d
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_fused_host_pinned_in_place_and_pageable_staged(lib, dtype):
+    """lcp_fused_host: pinned members read in place by the statistics kernel,
+    pageable members through a device staging copy; both give the device-resident
+    result bit for bit, with and without the mask, and again after the shape
+    changes (the staging buffers are rebuilt)."""
+    for h, w, m in ((61, 97, 7), (40, 33, 3)):
+        d = _fields(h, w, m, seed=h + m, k=3)
+        u = torch.from_numpy(d["u"]).to(dtype)
+        v = torch.from_numpy(d["v"]).to(dtype)
+        ref, ref_mask = lib.lcp_fused_ws(u.cuda(), v.cuda(), d["isovalues"], mask=True)
+        ref, ref_mask = ref.cpu(), ref_mask.cpu()
+        for pinned in (True, False):
+            uh, vh = (u.pin_memory(), v.pin_memory()) if pinned else (u.clone(), v.clone())
+            assert uh.is_pinned() == pinned
+            mh = torch.empty(ref_mask.shape, dtype=torch.int32).pin_memory()
+            out, mask = lib.lcp_fused_host(uh, vh, d["isovalues"], mask_host=mh)
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref) and torch.equal(mask, ref_mask)
+            out2, none = lib.lcp_fused_host(uh, vh, d["isovalues"])
+            torch.cuda.synchronize()
+            assert none is None and torch.equal(out2, ref)
+    assert lib.lcp_device_status(reset=True) == 0
