@@ -503,15 +503,11 @@ def lcp_member_contours(u, v, isovalues, dx: float = 1.0, dy: float = 1.0, capac
     return _contour_call(launch, m, h, w, k, u.device, capacity, keys, out)
 
 
-class _HostStaging:
-    """Device buffers reused by ``lcp_fused_host`` across calls of one shape."""
-
-    def __init__(self):
-        self.key = None
-        self.bufs = None
-
-
-_STAGING = _HostStaging()
+# Device buffers of ``lcp_fused_host``, one set per (device, stream), reused
+# while the shape, dtype, isovalue count, mask flag and input mode stay the same:
+# calls on one stream are ordered, so they may share them; other streams get
+# their own.
+_STAGING = {}
 
 
 def lcp_fused_host(u_host, v_host, isovalues, dx: float = 1.0, dy: float = 1.0, ddof: int = 1,
@@ -536,15 +532,17 @@ def lcp_fused_host(u_host, v_host, isovalues, dx: float = 1.0, dy: float = 1.0, 
     if dev.index is None:
         dev = torch.device("cuda", torch.cuda.current_device())
     in_place = u_host.is_pinned() and v_host.is_pinned()
-    key = (tuple(u_host.shape), u_host.dtype, k, mask_host is not None, str(dev), in_place)
-    if _STAGING.key != key:
-        _STAGING.bufs = (None if in_place else torch.empty_like(u_host, device=dev),
-                         None if in_place else torch.empty_like(v_host, device=dev),
-                         torch.empty((k, h - 1, w - 1), dtype=torch.float32, device=dev),
-                         torch.empty((k, h - 1, mask_words_per_row(w)), dtype=torch.int32, device=dev)
-                         if mask_host is not None else None)
-        _STAGING.key = key
-    ud, vd, od, md = _STAGING.bufs
+    slot = (str(dev), torch.cuda.current_stream(dev).cuda_stream)
+    key = (tuple(u_host.shape), u_host.dtype, k, mask_host is not None, in_place)
+    cached = _STAGING.get(slot)
+    if cached is None or cached[0] != key:
+        cached = (key, (None if in_place else torch.empty_like(u_host, device=dev),
+                        None if in_place else torch.empty_like(v_host, device=dev),
+                        torch.empty((k, h - 1, w - 1), dtype=torch.float32, device=dev),
+                        torch.empty((k, h - 1, mask_words_per_row(w)), dtype=torch.int32, device=dev)
+                        if mask_host is not None else None))
+        _STAGING[slot] = cached
+    ud, vd, od, md = cached[1]
     if in_place:
         lib = load()
         code = _dtype_code(u_host.dtype)
