@@ -426,3 +426,17 @@ def test_empirical_mc_converges_to_exact_empirical_lcp():
 
 def test_sse_definition():
     assert O.sum_squared_error([[0.5, 0.25]], [[0.25, 0.25]]) == 0.0625
+
+
+def test_stencil_neighbours_boundary_rule_by_hand():
+    """Sec. 3.1 boundary rule (reading R2), written out for small axes: central
+    neighbours (i-1, i+1) inside, first-order one-sided (0, 1) and (n-2, n-1) at
+    the two ends, so the index distance is 2 inside and 1 at the ends."""
+    lo, hi, steps = O.stencil_neighbours(2)
+    assert lo.tolist() == [0, 0] and hi.tolist() == [1, 1] and steps.tolist() == [1, 1]
+    lo, hi, steps = O.stencil_neighbours(5)
+    assert lo.tolist() == [0, 0, 1, 2, 3]
+    assert hi.tolist() == [1, 2, 3, 4, 4]
+    assert steps.tolist() == [1, 2, 2, 2, 1]
+    with pytest.raises(ValueError):
+        O.stencil_neighbours(1)
