@@ -51,3 +51,17 @@ def test_pack_rgba_and_default_stops():
     t = [s[0] for s in B.DEFAULT_STOPS]
     assert t[0] == 0.0 and t[-1] == 1.0 and all(a < b for a, b in zip(t, t[1:]))
     assert all(0.0 <= c <= 1.0 for s in B.DEFAULT_STOPS for c in s)
+
+
+def test_fused_host_wrapper_checks():
+    """lcp_fused_host takes host tensors [M, H, W] of one shape and dtype,
+    contiguous, and checks them before any CUDA call."""
+    u = cpu(3, 4, 5)
+    with pytest.raises(ValueError):
+        B.lcp_fused_host(u, cpu(3, 4, 6), [0.0])  # shapes differ
+    with pytest.raises(ValueError):
+        B.lcp_fused_host(u, cpu(3, 4, 5, dtype=torch.bfloat16), [0.0])  # dtypes differ
+    with pytest.raises(ValueError):
+        B.lcp_fused_host(cpu(4, 5), cpu(4, 5), [0.0])  # not [M, H, W]
+    with pytest.raises(ValueError):
+        B.lcp_fused_host(u.transpose(1, 2), u.transpose(1, 2), [0.0])  # not contiguous
