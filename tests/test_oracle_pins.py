@@ -274,6 +274,17 @@ def test_below_above_use_the_right_tail():
 # --------------------------------------------------------------------------
 # Philox-4x32-10 and Box-Muller
 # --------------------------------------------------------------------------
+def test_philox_published_known_answer_vectors():
+    """The generator's published known-answer vectors (Random123, SC'11):
+    counter and key in, four output words, bit for bit."""
+    kat = json.load(open(os.path.join(GOLDEN, "philox4x32_10_kat.json")))
+    for vec in kat["vectors"]:
+        ctr = np.array([[int(x, 16) for x in vec["counter"]]], dtype=np.uint32)
+        key = tuple(int(x, 16) for x in vec["key"])
+        got = O.philox4x32_10(ctr, key)[0]
+        assert [int(x) for x in got] == [int(x, 16) for x in vec["output"]]
+
+
 def test_philox_matches_independent_implementation():
     """Pin against Triton's open-source Philox-4x32-10 run in its CPU interpreter."""
     os.environ.setdefault("TRITON_INTERPRET", "1")
