@@ -206,3 +206,30 @@ def test_fused_band_rows_keep_one_band_when_the_workspace_is_exact(clib):
     assert rows(8192, 8192, 64 << 20) == 248  # the static 64 MiB scratch of lcp_fused_static_ws
     assert rows(8192, 8192, 11 * 8192 * 32 - 1) == 0  # below 8 rows plus 3 halo/record rows
     assert rows(1, 8192, full) == 0 and rows(8192, 8192, 0) == 0
+
+
+def test_volume_ring_and_contour_workspace_sizes(clib):
+    """Host arithmetic of the 3D ring and the contour scratch.  The ring holds
+    2B + 3 z-planes of 48-byte records (u, v, w per vertex): B new planes per
+    slab (as many as fit a 96 MB budget, at least 1, at most D) plus the 3
+    planes the next slab re-reads."""
+    ws3 = clib.lcp3d_workspace_bytes
+    plane = lambda h, w: h * w * 48  # noqa: E731
+    # 256^2 planes: 3.1 MB each, 32 fit in 96 MB -> B = 14, a 31-plane ring
+    assert ws3(20, 256, 256, 256, 0) == 31 * plane(256, 256)
+    # 256 x 683: 8.4 MB planes, 11 fit -> B = 4, an 11-plane ring
+    assert ws3(3, 9, 256, 683, 0) == 11 * plane(256, 683)
+    # tiny volumes: B is capped at D
+    assert ws3(1, 2, 2, 2, 0) == (2 * 2 + 3) * plane(2, 2)
+    assert ws3(4, 5, 7, 40, 1) == (2 * 5 + 3) * plane(7, 40)
+    # planes too large for 5 in the budget still get B = 1 (a 5-plane ring)
+    assert ws3(2, 64, 1024, 1024, 0) == 5 * plane(1024, 1024)
+    for bad in ((1, 1, 4, 4), (1, 4, 1, 4), (1, 4, 4, 1)):
+        assert ws3(*bad, 0) == 0
+    wsc = clib.lcp_contours_workspace_bytes
+    assert wsc(0, 4, 4) == 0 and wsc(1, 1, 4) == 0 and wsc(1, 4, 1) == 0
+    prev = 0
+    for m, h, w in ((1, 2, 2), (1, 97, 131), (51, 721, 1440)):
+        n = wsc(m, h, w)
+        assert n >= 264 and (n - 256) % 8 == 0 and n > prev  # header + one 8-byte descriptor per tile
+        prev = n
