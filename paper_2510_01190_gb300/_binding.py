@@ -515,7 +515,9 @@ def lcp_fused_host(u_host, v_host, isovalues, dx: float = 1.0, dy: float = 1.0, 
     """End-to-end call for host-resident ensembles [M, H, W] (fp32 or bf16).
     Pinned members are read in place by the statistics kernel of
     ``lcp_fused_ws`` over the CPU-GPU link, each byte once, with no staging
-    copy; pageable ones are first copied into a device staging buffer.  The
+    copy (torch's pinned memory comes from cudaHostAlloc, whose pointers a
+    kernel may use directly under unified addressing); pageable ones are first
+    copied into a device staging buffer.  The
     LCP map (and the mask words, if ``mask_host`` is given) is copied back into
     the host outputs (pinned ones asynchronously), all on the current stream.
     Returns (out_host, mask_host); the results are complete, and the members
