@@ -93,6 +93,20 @@ def test_product_package_never_reaches_the_oracle():
                 assert "lcp_oracle" not in src, f
 
 
+def test_oracle_never_reaches_the_product_package():
+    """The oracle shares no code with the CUDA path: its modules import only the
+    standard library, numpy, scipy and each other, never the product package."""
+    allowed = {"__future__", "math", "numpy", "scipy"}
+    odir = os.path.join(ROOT, "oracle")
+    for f in sorted(os.listdir(odir)):
+        if not f.endswith(".py"):
+            continue
+        src = open(os.path.join(odir, f)).read()
+        for m in re.finditer(r"^\s*(?:import|from)\s+([A-Za-z_.][A-Za-z0-9_.]*)", src, flags=re.M):
+            mod = m.group(1)
+            assert mod.startswith(".") or mod.split(".")[0] in allowed, (f, mod)
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     from paper_2510_01190_gb300 import _binding
 
