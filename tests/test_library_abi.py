@@ -107,6 +107,16 @@ def test_oracle_never_reaches_the_product_package():
             assert mod.startswith(".") or mod.split(".")[0] in allowed, (f, mod)
 
 
+def test_input_generators_stand_apart_from_both_sides():
+    """The seeded input generators, the one module that the oracle's tests and
+    the CUDA path's tests share, import neither the library binding nor the
+    oracle."""
+    src = open(os.path.join(ROOT, "paper_2510_01190_gb300", "synth.py")).read()
+    mods = {m.group(1).split(".")[0]
+            for m in re.finditer(r"^\s*(?:import|from)\s+([A-Za-z_.][A-Za-z0-9_.]*)", src, flags=re.M)}
+    assert mods <= {"__future__", "math", "numpy", "torch", "statistics"}, mods
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     from paper_2510_01190_gb300 import _binding
 
