@@ -178,15 +178,18 @@ lcp_status lcp_fused_ws(const void* u, const void* v, lcp_dtype in_dtype, int M,
  * allocates no memory: for callers that hold no device allocator, or that must
  * not pay an allocation's device synchronisation (or its failure under memory
  * pressure) inside a steady-state loop.  The paper has no counterpart: it is a
- * host-interface convenience around the same computation (Eqs. 1-3 and the LCP
- * of Sec. 3.2), with the same arguments and results as lcp_fused_ws.
- * Set-up: the first call on each device (with that device current) looks up
- * the array's device address; make that first call before any stream capture.
+ * host-interface convenience that computes the same results as lcp_fused_ws,
+ * with the same arguments except the workspace.
+ * Set-up: every call looks up the array's device address on the current
+ * device (after cudaDeviceReset the module may load at another address); the
+ * first call on a device loads the library's module there, so make that first
+ * call before any stream capture.
  * The per-band counters that must start at zero are cleared on `stream` by
  * every call.  The one array is shared by all calls on a device: calls that
  * overlap in time (other streams, other host threads) race and give undefined
  * results.  The row bands shrink to fit the 64 MiB (wide grids run in more,
- * smaller bands than with lcp_fused_workspace_bytes of workspace).  Errors:
+ * smaller bands than with lcp_fused_workspace_bytes of workspace: an
+ * 8192-wide grid in 248-row bands instead of 376).  Errors:
  * LCP_ERR_ARG when even the smallest band (8 cell rows plus the halo) needs more
  * than 64 MiB (grids wider than about 190,000 vertices) or on any argument
  * lcp_fused_ws rejects; LCP_ERR_CUDA when the address lookup fails.
@@ -199,7 +202,7 @@ lcp_status lcp_fused_static_ws(const void* u, const void* v, lcp_dtype in_dtype,
  * Batched closed form: many fields of uneven size (each its own H, W, M,
  * spacing and isovalue list) evaluated by ONE persistent kernel launch.  The
  * computation per field is exactly lcp_fused's (Eqs. 1-3 per vertex, the LCP of
- * Sec. 3.2 per cell and isovalue, the mean-field mask); the paper evaluates one
+ * Sec. 3.1's last paragraph per cell and isovalue, the mean-field mask); the paper evaluates one
  * field at a time, and batching is this library's addition.
  *
  * lcp_field_desc - one field of a batch (all pointers are device pointers owned
@@ -434,14 +437,55 @@ lcp_status lcp_mc(lcp_mc_mode mode, const float* mu_u, const float* var_u, const
  * lcp_device_status - read (and optionally clear) the library's device status
  * word on the current device.  Bit 0 is set when a bounded device-side wait
  * (the TMA pipeline's mbarrier waits, the workspace path's waits for
- * statistics rows) gave up; the affected outputs are then undefined.  This
- * call synchronises with the device.
+ * statistics rows) gave up; the affected outputs are then undefined (an LCP
+ * block of the workspace path whose wait gave up writes NaN into its cells and
+ * clears its mask bits instead of reading incomplete statistics).  This call
+ * synchronises with the device.
  * Bit 1: a wait of the learned-surrogate inference (tcgen05 mbarrier) gave up.
  * Bit 2: a contour look-back wait gave up.
  * Returns LCP_ERR_TIMEOUT if any bit is set, LCP_OK otherwise; `flags` (host,
  * may be NULL) receives the word; `reset` != 0 clears it.
  */
 lcp_status lcp_device_status(uint32_t* flags, int reset);
+
+/*
+ * lcp_set_wait_budget - the clock-cycle budget after which a bounded device
+ * wait gives up: the workspace path's LCP blocks waiting for their statistics
+ * rows (lcp_fused_ws, lcp_fused_static_ws, lcp_speed_gradient_ws) and the
+ * contour look-back (lcp_contours, lcp_member_contours).  The budget is read
+ * on the host at every launch and passed to the kernel.  `cycles` <= 0
+ * restores the default, 4e9 cycles (about 2 s at 2 GHz).  Returns the budget in
+ * force before the call.  Process-wide; not a property of the paper's method
+ * (these waits exist because this library overlaps its kernels).  The TMA
+ * pipeline's and the learned inference's mbarrier waits keep a fixed budget of
+ * the same size.
+ */
+long long lcp_set_wait_budget(long long cycles);
+
+/*
+ * Failure-path probes.  Each launches one of the library's waiting kernels
+ * against a flag that nothing in the launch will ever set, so that its bounded
+ * wait must run out (use a small lcp_set_wait_budget first); the kernel then
+ * sets its bit of lcp_device_status and finishes.  They exist to test the
+ * timeout path without a faulty producer; the paper has no counterpart.
+ *
+ * lcp_test_stalled_lcp_wait - the LCP kernels of lcp_fused_ws for the cells of
+ * the workspace layout's first row band, waiting on that band's statistics
+ * counters, which it clears and no statistics kernel releases.  Arguments as
+ * lcp_fused_ws's (no members).  Every cell of the band receives NaN and its
+ * mask bits 0; lcp_device_status then reports bit 0.
+ *
+ * lcp_test_stalled_lookback - lcp_contours with the first tile's ticket never
+ * handed out: the tile that takes ticket 1 waits for tile 0's look-back flag,
+ * which no tile writes.  Needs at least two tiles (more than 992 cells).  The
+ * segments of tile 0's cells are missing and the others placed as if tile 0
+ * had none; lcp_device_status then reports bit 2.
+ */
+lcp_status lcp_test_stalled_lcp_wait(int H, int W, const float* iso, int K, void* lcp_out, lcp_dtype out_dtype,
+                                     uint32_t* mask, void* workspace, size_t workspace_bytes, lcp_stream_t stream);
+lcp_status lcp_test_stalled_lookback(const float* field, int H, int W, const float* iso, int K, float* seg,
+                                     long long* key, int64_t capacity, unsigned long long* count, void* workspace,
+                                     size_t workspace_bytes, lcp_stream_t stream);
 
 /*
  * lcp_speed_gradient - the preprocessing of the Red Sea study (Sec. 4.2,
@@ -573,7 +617,8 @@ lcp_status lcp_member_contours(const void* u, const void* v, lcp_dtype in_dtype,
  *
  * values  device fp32 [planes][rows][cols] (contiguous), e.g. an LCP map
  *         [K][H-1][W-1]
- * vmin, vmax   display range, finite, vmin < vmax
+ * vmin, vmax   display range, finite, vmin < vmax, with vmax - vmin finite
+ *         in fp32 (below about 3.4e38)
  * stops   HOST array of n_stops x 5 floats (t, r, g, b, a), every entry in
  *         [0, 1], t strictly increasing from exactly 0 to exactly 1;
  *         2 <= n_stops <= LCP_MAX_COLOR_STOPS
@@ -583,19 +628,17 @@ lcp_status lcp_member_contours(const void* u, const void* v, lcp_dtype in_dtype,
  *         bit paints mask_rgba (the mean-field contour cells, Fig. 1a)
  * rgba    device uint8 [planes][rows][cols][4], bytes r, g, b, a per value
  *
- * Every operation below is a single IEEE fp32 operation rounded to nearest
- * (no fused multiply-add), so that any fp32 implementation of these steps
- * produces the same bytes.  Once per call:
- *   R = 1 / (vmax - vmin);  per stop segment s < n_stops - 1:
- *   r_s = 1 / (t_{s+1} - t_s),  d_s = c_{s+1} - c_s   (each of r, g, b, a)
- * then per value x:
- *   x NaN -> nan_rgba; else if the mask bit is set -> mask_rgba; else
- *   t  = min(max((x - vmin) * R, 0), 1)
- *   s  = the largest stop index <= n_stops - 2 with t_s <= t
- *   f  = (t - t_s) * r_s
- *   ch = c_s + f * d_s                               for each of r, g, b, a
- *   byte = min(max(floor(ch * 255 + 0.5), 0), 255)
- * where max and min return the non-NaN operand (IEEE maxNum / minNum).
+ * The map (the mathematics): per value x, NaN -> nan_rgba; else if the mask
+ * bit is set -> mask_rgba; else t = clamp((x - vmin) / (vmax - vmin), 0, 1)
+ * (+inf -> 1, -inf -> 0), s = the largest stop index <= n_stops - 2 with
+ * t_s <= t, ch = c_s + (t - t_s) / (t_{s+1} - t_s) (c_{s+1} - c_s) for each of
+ * r, g, b, a, byte = floor(255 ch + 1/2).
+ * The kernel evaluates it in fp32: R = 1 / (vmax - vmin), r_s = 1 / (t_{s+1} -
+ * t_s) and d_s = c_{s+1} - c_s once per call, then t = clamp((x - vmin) R),
+ * f = (t - t_s) r_s, ch = c_s + f d_s, each one operation rounded to nearest.
+ * A byte therefore equals the exact one except where 255 ch + 1/2 lies within
+ * about 2^-24 (255 (4 |d_s| r_s + 6 |d_s| + 2) + 512) of an integer, where it
+ * can differ by one.
  * Alignment: values, mask and rgba 4-byte aligned (16 bytes gives vector
  * access).  Errors: LCP_ERR_ARG for a negative size, NULL pointers (n > 0),
  * a bad range or stop table, or misalignment.  planes * rows * cols == 0 is a

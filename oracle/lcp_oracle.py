@@ -19,7 +19,7 @@ Conventions (shared with the GPU library by documentation, not by code)
 * Cell ``(i, j)`` has the vertices ``(i, j), (i+1, j), (i, j+1), (i+1, j+1)``;
   LCP maps are ``[K, H-1, W-1]`` for ``K`` isovalues.
 
-Readings taken where the paper is silent (each is listed in the design doc)
+Readings taken where the paper is silent
 ----------------------------------------------------------------------
 R1  LCP (Sec. 3.1 cites Poethkow et al. without printing the formula): with
     independent vertex values, P(crossing) = 1 - prod_k P(D_k < c)

@@ -20,7 +20,7 @@ numpy, so that the GPU kernels can be checked against it:
 Only ``tests/``, ``__graft_entry__.smoke`` and ``bench.py``'s CPU-baseline leg
 may import this module.  It imports nothing from the GPU library.
 
-Readings (listed in DESIGN.md)
+Readings
 ------------------------------
 R14 Features of cell (i, j), isovalue c, vertices in the order (i, j),
     (i+1, j), (i, j+1), (i+1, j+1), each with divergence cumulants k1..k4,

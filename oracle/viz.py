@@ -3,32 +3,33 @@
 The paper (arXiv 2510.01190) shows its results as colour-mapped LCP maps
 (Sec. 3.1, last paragraph), the mean-field divergence with its isocontour
 (Fig. 1a, Fig. 3c, clamped to a display range in Sec. 4.2), and spaghetti plots
-of the isocontours of every ensemble member (Fig. 1b).  This module fixes what
-the GPU library computes for those outputs:
+of the isocontours of every ensemble member (Fig. 1b).  This module states
+those outputs as mathematics, in FP64 with true divisions:
 
-* ``colormap_rgba``: the piecewise-linear colour map of reading R17, step by
-  step in IEEE fp32 (a quantised code: both sides decide it in the kernel's
-  precision);
+* ``colormap_levels`` / ``colormap_rgba``: the piecewise-linear colour map of
+  reading R17;
 * ``marching_squares``: the isocontour segments of a scalar field on the grid
-  (reading R18), in FP64 except for the two decisions R18 fixes in fp32;
-* ``member_divergence32`` and ``spaghetti_contours``: every member's Eq. 1
-  divergence in fp32 (the operation order of reading R18) and its isocontours,
-  the spaghetti plot of Fig. 1b.
+  (reading R18);
+* ``spaghetti_contours``: the isocontours of every member's Eq. 1 divergence
+  (``lcp_oracle.divergence_of_field``, FP64), the spaghetti plot of Fig. 1b.
+
+A GPU kernel computing these in fp32 can differ from them only where fp32
+rounding moves a quantity across a decision threshold (a byte boundary, an
+isovalue, the saddle centre); the parity tests state those guard bands.
 
 Only ``tests/``, ``__graft_entry__.smoke`` and ``bench.py``'s CPU-baseline leg
 may import this module.  It imports nothing from the GPU library.
 
-Readings (listed in DESIGN.md)
-------------------------------
-R17 Colour map (the paper names none): a table of stops (t, r, g, b, a) with
-    t from 0 to 1; t = clamp((x - vmin) R, 0, 1) with R = 1 / (vmax - vmin);
-    linear interpolation inside the stop segment s that holds t, as
-    f = (t - t_s) r_s and ch = c_s + f d_s with r_s = 1 / (t_{s+1} - t_s) and
-    d_s = c_{s+1} - c_s formed once per table; byte = floor(255 ch + 0.5).
-    Every step is one fp32 operation rounded to nearest.  NaN values get their
-    own colour; an optional crossing mask paints the mean-field contour cells
-    in a contour colour (the black / cyan contour of Fig. 1a / Fig. 3c at cell
-    resolution).
+Readings
+--------
+R17 Colour map (the paper names none): a table of stops (t_q, r_q, g_q, b_q,
+    a_q), q = 0..S-1, with t_0 = 0 < t_1 < ... < t_{S-1} = 1.  A value x maps to
+    t = clamp((x - vmin) / (vmax - vmin), 0, 1) (x = +inf gives 1, -inf 0);
+    the segment s is the largest q <= S-2 with t_q <= t; inside it each
+    channel is ch = c_s + (t - t_s) / (t_{s+1} - t_s) (c_{s+1} - c_s) and the
+    byte is floor(255 ch + 1/2).  NaN values get their own colour; an optional
+    crossing mask paints the mean-field contour cells in a contour colour (the
+    black / cyan contour of Fig. 1a / Fig. 3c at cell resolution), except NaN.
 R18 Isocontour segments (marching squares; the paper shows mean-field
     isocontours in Fig. 1a / Fig. 3c and spaghetti plots of the members'
     isocontours in Fig. 1b without defining the extraction).  Cell (i, j) has
@@ -39,25 +40,24 @@ R18 Isocontour segments (marching squares; the paper shows mean-field
     x = i + (c - f(i, j)) / (f(i+1, j) - f(i, j)), on a vertical one
     y = j + (c - f(i, j)) / (f(i, j+1) - f(i, j)), so neighbouring cells agree
     on shared points.  Two crossing edges give one segment (lower edge first).
-    The saddles (v0, v2 on one side, v1, v3 on the other) give two: if the
-    centre value ((f0 + f1) + (f2 + f3)) / 4, formed in fp32, lies on v0's side,
-    (E0, E1) and (E2, E3), else (E0, E3) and (E1, E2).  Cells with a NaN corner
-    give none.  Segment (x0, y0, x1, y1) carries the key
-    ((j (W-1) + i) K + k) 2 + s (s = 0, 1 within the cell); for member m of a
-    spaghetti plot the key adds m (H-1)(W-1) K 2.  Lists are in key order.
-    The member divergence of a spaghetti plot is Eq. 1 in fp32 with each
-    operation rounded: (u[i+] - u[i-]) * sx + (v[j+] - v[j-]) * sy with
-    sx = fp32(1 / ((i+ - i-) dx)) (likewise sy), so that the crossing
-    decisions are the kernel's.
+    The saddles (v0, v2 on one side, v1, v3 on the other) give two, decided by
+    the cell's centre value (f0 + f1 + f2 + f3) / 4, the bilinear interpolant
+    at the cell centre: if it lies on v0's side, (E0, E1) and (E2, E3), else
+    (E0, E3) and (E1, E2).  Cells with a NaN corner give none.  Segment
+    (x0, y0, x1, y1) carries the key ((j (W-1) + i) K + k) 2 + s (s = 0, 1
+    within the cell); for member m of a spaghetti plot the key adds
+    m (H-1)(W-1) K 2.  Lists are in key order.  A spaghetti plot contours each
+    member's divergence as Eq. 1 defines it (central differences inside,
+    first-order one-sided differences on the first and last row and column).
 """
 
 from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["colormap_rgba", "pack_rgba", "marching_squares", "member_divergence32", "spaghetti_contours"]
+from . import lcp_oracle as _core
 
-_F = np.float32
+__all__ = ["colormap_levels", "colormap_rgba", "pack_rgba", "marching_squares", "spaghetti_contours"]
 
 
 def pack_rgba(r: int, g: int, b: int, a: int) -> int:
@@ -65,14 +65,34 @@ def pack_rgba(r: int, g: int, b: int, a: int) -> int:
     return int(r) | (int(g) << 8) | (int(b) << 16) | (int(a) << 24)
 
 
-def _quantise(ch):
-    b = np.floor((ch * _F(255.0)).astype(_F) + _F(0.5)).astype(_F)
-    return np.clip(b, 0, 255).astype(np.uint8)
+def _unpack(word: int):
+    return np.array([(int(word) >> (8 * k)) & 0xFF for k in range(4)], dtype=np.uint8)
+
+
+def colormap_levels(values, vmin: float, vmax: float, stops):
+    """Reading R17 before quantisation, in FP64: returns (y, s) where
+    y [..., 4] = 255 ch + 1/2 of every channel (its floor is the byte) and
+    s [...] is the stop segment of each value (NaN values: y is NaN, s = 0)."""
+    x = np.asarray(values, dtype=np.float64)
+    st = np.asarray(stops, dtype=np.float64).reshape(-1, 5)
+    n_stops = st.shape[0]
+    lo, hi = float(vmin), float(vmax)
+    with np.errstate(invalid="ignore", over="ignore"):
+        t = (x - lo) / (hi - lo)
+        t = np.where(np.isnan(t), np.nan, np.clip(t, 0.0, 1.0))
+        s = np.zeros(x.shape, dtype=np.int64)
+        for q in range(1, n_stops - 1):
+            s = np.where(t >= st[q, 0], q, s)
+        f = (t - st[s, 0]) / (st[s + 1, 0] - st[s, 0])
+        y = np.empty(x.shape + (4,), dtype=np.float64)
+        for ch in range(4):
+            c = st[s, 1 + ch] + f * (st[s + 1, 1 + ch] - st[s, 1 + ch])
+            y[..., ch] = 255.0 * c + 0.5
+    return y, s
 
 
 def colormap_rgba(values, vmin: float, vmax: float, stops, nan_rgba: int = 0, mask=None, mask_rgba: int = 0):
-    """RGBA8 colour of every value (reading R17), in IEEE fp32 one operation
-    at a time (numpy rounds each float32 operation to nearest).
+    """RGBA8 colour of every value (reading R17), in FP64.
 
     values : float array [..., rows, cols]
     stops  : [S, 5] (t, r, g, b, a)
@@ -80,55 +100,34 @@ def colormap_rgba(values, vmin: float, vmax: float, stops, nan_rgba: int = 0, ma
              ``mask_rgba``)
     returns uint8 [..., rows, cols, 4]
     """
-    x = np.asarray(values, dtype=_F)
-    st = np.asarray(stops, dtype=_F).reshape(-1, 5)
-    n_stops = st.shape[0]
-    lo, hi = _F(vmin), _F(vmax)
-    one = _F(1.0)
-    with np.errstate(invalid="ignore", over="ignore"):
-        big_r = one / (hi - lo)                               # R (0 when the range overflows)
-        r_seg = one / (st[1:, 0] - st[:-1, 0])                # r_s
-        d_seg = st[1:, 1:] - st[:-1, 1:]                      # d_s, [n_stops - 1, 4]
-        t = ((x - lo).astype(_F) * big_r).astype(_F)
-        t = np.fmin(np.fmax(t, _F(0.0)), _F(1.0))  # maxNum / minNum: a NaN operand yields the other
-        s = np.zeros(x.shape, dtype=np.int64)
-        for q in range(1, n_stops - 1):
-            s = np.where(t >= st[q, 0], q, s)
-        f = ((t - st[s, 0]).astype(_F) * r_seg[s]).astype(_F)
-        out = np.empty(x.shape + (4,), dtype=np.uint8)
-        for ch in range(4):
-            c = (st[s, 1 + ch] + (f * d_seg[s, ch]).astype(_F)).astype(_F)
-            out[..., ch] = _quantise(c)
-    nan_bytes = np.array([(nan_rgba >> (8 * k)) & 0xFF for k in range(4)], dtype=np.uint8)
-    out[np.isnan(x)] = nan_bytes
+    x = np.asarray(values, dtype=np.float64)
+    y, _ = colormap_levels(x, vmin, vmax, stops)
+    nan = np.isnan(x)
+    with np.errstate(invalid="ignore"):
+        out = np.clip(np.floor(np.where(nan[..., None], 0.0, y)), 0, 255).astype(np.uint8)
+    out[nan] = _unpack(nan_rgba)
     if mask is not None:
-        m = np.asarray(mask, dtype=bool) & ~np.isnan(x)
-        out[m] = np.array([(mask_rgba >> (8 * k)) & 0xFF for k in range(4)], dtype=np.uint8)
+        m = np.asarray(mask, dtype=bool) & ~nan
+        out[m] = _unpack(mask_rgba)
     return out
 
 
 # --------------------------------------------------------------------------
 # Isocontour segments (reading R18)
 # --------------------------------------------------------------------------
-def _centre32(f0, f1, f2, f3):
-    """The saddle decider's centre value in fp32: ((f0 + f1) + (f2 + f3)) * 0.25."""
-    a = (np.float32(f0) + np.float32(f1)).astype(_F)
-    b = (np.float32(f2) + np.float32(f3)).astype(_F)
-    return ((a + b).astype(_F) * _F(0.25)).astype(_F)
-
-
 def marching_squares(f, isovalues):
     """Isocontour segments of the scalar field f [H, W] for every isovalue
-    (reading R18).  returns (keys int64 [n], segs float64 [n, 4]) in key order."""
+    (reading R18), in FP64.  returns (keys int64 [n], segs float64 [n, 4]) in
+    key order."""
     f = np.asarray(f, np.float64)
     h, w = f.shape
-    iso = np.atleast_1d(np.asarray(isovalues, np.float32))
+    iso = np.atleast_1d(np.asarray(isovalues, np.float64))
     kk = iso.size
     f0, f1 = f[:-1, :-1], f[:-1, 1:]      # v0 = (i, j), v1 = (i+1, j)
     f3, f2 = f[1:, :-1], f[1:, 1:]        # v3 = (i, j+1), v2 = (i+1, j+1)
     jj, ii = np.meshgrid(np.arange(h - 1, dtype=np.float64), np.arange(w - 1, dtype=np.float64), indexing="ij")
     finite = ~(np.isnan(f0) | np.isnan(f1) | np.isnan(f2) | np.isnan(f3))
-    cen = _centre32(f0, f1, f2, f3).astype(np.float64)
+    centre = (f0 + f1 + f2 + f3) / 4.0
     cell = (np.arange(h - 1)[:, None] * (w - 1) + np.arange(w - 1)[None, :]).astype(np.int64)
     keys, segs = [], []
     with np.errstate(invalid="ignore", divide="ignore"):
@@ -151,7 +150,7 @@ def marching_squares(f, isovalues):
                     keys.append(((cell[sel] * kk + k) * 2).ravel())
                     segs.append(np.concatenate([p[a][sel], p[b][sel]], -1))
             # saddles: the centre on v0's side joins v0 and v2
-            with_v0 = saddle & ((cen < c) == b0)
+            with_v0 = saddle & ((centre < c) == b0)
             for sel, pairs in ((with_v0, ((0, 1), (2, 3))), (saddle & ~with_v0, ((0, 3), (1, 2)))):
                 for s_idx, (a, b) in enumerate(pairs):
                     keys.append(((cell[sel] * kk + k) * 2 + s_idx).ravel())
@@ -162,27 +161,10 @@ def marching_squares(f, isovalues):
     return keys[order], segs[order].reshape(-1, 4)
 
 
-def member_divergence32(u, v, dx: float, dy: float):
-    """Eq. 1 divergence of every member in IEEE fp32 with the operation order of
-    reading R18.  u, v [M, H, W]; returns float32 [M, H, W]."""
-    u = np.asarray(u, _F)
-    v = np.asarray(v, _F)
-    _, h, w = u.shape
-    i = np.arange(w)
-    il, ih = np.maximum(i - 1, 0), np.minimum(i + 1, w - 1)
-    j = np.arange(h)
-    jl, jh = np.maximum(j - 1, 0), np.minimum(j + 1, h - 1)
-    sx = np.where(ih - il == 2, _F(0.5 / dx), _F(1.0 / dx)).astype(_F)[None, None, :]
-    sy = np.where(jh - jl == 2, _F(0.5 / dy), _F(1.0 / dy)).astype(_F)[None, :, None]
-    gx = ((u[:, :, ih] - u[:, :, il]).astype(_F) * sx).astype(_F)
-    gy = ((v[:, jh, :] - v[:, jl, :]).astype(_F) * sy).astype(_F)
-    return (gx + gy).astype(_F)
-
-
 def spaghetti_contours(u, v, dx: float, dy: float, isovalues):
-    """Isocontours of every member's divergence (Fig. 1b), reading R18.
-    returns (keys int64 [n], segs float64 [n, 4]) in key order."""
-    d = member_divergence32(u, v, dx, dy)
+    """Isocontours of every member's Eq. 1 divergence (Fig. 1b), reading R18.
+    u, v [M, H, W]; returns (keys int64 [n], segs float64 [n, 4]) in key order."""
+    d = _core.divergence_of_field(u, v, dx, dy)
     m, h, w = d.shape
     kk = np.atleast_1d(np.asarray(isovalues)).size
     per = (h - 1) * (w - 1) * kk * 2
@@ -191,4 +173,6 @@ def spaghetti_contours(u, v, dx: float, dy: float, isovalues):
         k_m, s_m = marching_squares(d[mm], isovalues)
         keys.append(k_m + mm * per)
         segs.append(s_m)
+    if not keys:
+        return np.zeros(0, np.int64), np.zeros((0, 4))
     return np.concatenate(keys), np.concatenate(segs)

@@ -53,6 +53,9 @@ __all__ = [
     "DEFAULT_STOPS",
     "pack_rgba",
     "lcp_device_status",
+    "lcp_set_wait_budget",
+    "lcp_test_stalled_lcp_wait",
+    "lcp_test_stalled_lookback",
     "mask_words_per_row",
     "unpack_mask",
     "LCP_F32",
@@ -138,6 +141,10 @@ _SIGNATURES = {
                              c_u32, c_vp, c_vp]),
     "lcp_fused_static_ws": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double, c_fp,
                                     c_int, c_vp, c_int, c_vp, c_vp]),
+    "lcp_set_wait_budget": (ctypes.c_longlong, [ctypes.c_longlong]),
+    "lcp_test_stalled_lcp_wait": (c_int, [c_int, c_int, c_fp, c_int, c_vp, c_int, c_vp, c_vp, ctypes.c_size_t, c_vp]),
+    "lcp_test_stalled_lookback": (c_int, [c_vp, c_int, c_int, c_fp, c_int, c_vp, c_vp, c_i64, c_vp, c_vp,
+                                          ctypes.c_size_t, c_vp]),
 }
 
 
@@ -623,6 +630,42 @@ def lcp_device_status(reset: bool = False) -> int:
     if status not in (0, -4):
         _check(status)
     return int(flags.value)
+
+
+def lcp_set_wait_budget(cycles: int) -> int:
+    """Clock-cycle budget of the bounded device waits that take it (0 restores
+    the default, ~2 s); returns the previous budget."""
+    return int(load().lcp_set_wait_budget(int(cycles)))
+
+
+def lcp_test_stalled_lcp_wait(h: int, w: int, isovalues, out, mask_out=None, workspace=None):
+    """Failure-path probe: the LCP kernels of the workspace path waiting on
+    statistics counters that nothing releases (``out`` float32/float16
+    [K, H-1, W-1], ``mask_out`` int32 words or None)."""
+    iso, k, iso_p = _iso(isovalues)
+    lib = load()
+    need = int(lib.lcp_fused_workspace_bytes(1, h, w, LCP_F32))
+    if workspace is None:
+        _, ws_ptr = _workspace(need, out.device)
+        ws_bytes = need
+    else:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    _check(lib.lcp_test_stalled_lcp_wait(h, w, iso_p, k, _ptr(out), _dtype_code(out.dtype), _ptr(mask_out),
+                                         c_vp(ws_ptr), ws_bytes, _stream()))
+    return out, mask_out
+
+
+def lcp_test_stalled_lookback(field, isovalues, capacity: int):
+    """Failure-path probe: lcp_contours with tile 0 never run, so the next
+    tile's look-back waits for a flag nothing sets.  Returns (seg, key, total)."""
+    h, w = field.shape
+    iso, k, iso_p = _iso(isovalues)
+
+    def launch(seg, key, cap, count, ws, nbytes):
+        return load().lcp_test_stalled_lookback(_ptr(field), h, w, iso_p, k, seg, key, cap, count, ws, nbytes,
+                                                _stream())
+
+    return _contour_call(launch, 1, h, w, k, field.device, capacity, True, None)
 
 
 def lcp_batch_workspace_bytes(n_fields: int, n_iso: int) -> int:

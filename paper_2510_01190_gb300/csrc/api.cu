@@ -3,11 +3,19 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "lcp_common.cuh"
 
 namespace lcp {
+
+static std::atomic<long long> g_wait_budget{0};  // 0: the default
+
+long long wait_budget_cycles() {
+    const long long b = g_wait_budget.load(std::memory_order_relaxed);
+    return b > 0 ? b : kDefaultWaitBudget;
+}
 
 static thread_local char g_last_error[512] = "";
 
@@ -67,6 +75,12 @@ extern "C" const char* lcp_status_string(lcp_status s) {
 extern "C" const char* lcp_last_error(void) { return g_last_error; }
 
 extern "C" int lcp_version(void) { return 10000; }
+
+extern "C" long long lcp_set_wait_budget(long long cycles) {
+    const long long prev = wait_budget_cycles();
+    g_wait_budget.store(cycles > 0 ? cycles : 0, std::memory_order_relaxed);
+    return prev;
+}
 
 extern "C" lcp_status lcp_philox_fill(uint64_t seed, uint32_t c1, uint64_t offset, int64_t count, uint32_t* out,
                                       lcp_stream_t stream) {

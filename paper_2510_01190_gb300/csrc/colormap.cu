@@ -7,11 +7,13 @@
 // under about 45 instructions per value to run at HBM speed.  Hence: each
 // thread maps 4 consecutive values (one 16-byte load and store when the
 // buffers allow it); the reciprocals and colour differences of every stop
-// segment are formed once per call on the host; the segment of a value is the
+// segment are formed once per call on the host (each value then costs
+// multiplications instead of two divisions; the bytes can differ from the
+// exact map by one where a channel lies within fp32 rounding of a byte
+// boundary); the segment of a value is the
 // count of stop positions at or below it, compared against registers; the four
 // channels are interpolated and quantised as two float2 pairs with Blackwell's
-// paired fp32 instructions (each half an IEEE rounded-to-nearest operation, so
-// the bytes equal those of the scalar steps the header fixes); the row and
+// paired fp32 instructions (each half an IEEE rounded-to-nearest operation); the row and
 // column of the mask bits advance with the grid stride instead of being
 // divided out, and one or two mask words serve a group of 4 values.
 #include <algorithm>
@@ -173,6 +175,12 @@ extern "C" lcp_status lcp_colormap(const float* values, int planes, int rows, in
     const int64_t n = (int64_t)planes * rows * cols;
     if (!(std::isfinite(vmin) && std::isfinite(vmax) && vmin < vmax))
         return fail(LCP_ERR_ARG, "%s: need finite vmin < vmax", fn);
+    {
+        volatile float lo = vmin, hi = vmax;
+        volatile float range = hi - lo;
+        if (!std::isfinite((float)range))
+            return fail(LCP_ERR_ARG, "%s: vmax - vmin overflows fp32", fn);
+    }
     if (!stops || n_stops < 2 || n_stops > LCP_MAX_COLOR_STOPS)
         return fail(LCP_ERR_ARG, "%s: need a host array of 2..%d stops", fn, LCP_MAX_COLOR_STOPS);
     for (int q = 0; q < n_stops; ++q) {

@@ -3,9 +3,9 @@
 // spaghetti plot of Fig. 1b -- compacted into one segment list in key order in
 // a single pass.
 //
-// A tile of 256 threads takes a ticket (its position in start order) and 1984
+// A tile of 256 threads takes a ticket (its position in start order) and 992
 // consecutive items (cells, or member cells); in round e lane l < 31 of warp w
-// takes item 248 w + 31 e + l, so that the segments of one round fill one
+// takes item 124 w + 31 e + l, so that the segments of one round fill one
 // contiguous output range in lane order and the warp's stores coalesce; the
 // right corners of a cell are the next lane's left ones, by shuffle (lane 31
 // evaluates the 32nd corner column).  Per
@@ -19,7 +19,7 @@
 // reads the flags of the 32 preceding tiles at a time until it meets one that
 // holds an inclusive prefix.  Every tile it waits for took its ticket earlier,
 // so it is running and publishes without waiting itself; each wait is still
-// bounded (~2 s of clock), after which the tile counts the missing flag as 0,
+// bounded (lcp_set_wait_budget, ~2 s of clock by default), after which the tile counts the missing flag as 0,
 // sets a bit in the library's device status and carries on.  Then each warp
 // lays a round's segments out in shared memory as small descriptors in their
 // final order, shares them evenly among its lanes (a cell can have up to 2K
@@ -28,8 +28,11 @@
 // members out of L2): in key order, the same on every run.
 //
 // The member divergence uses Eq. 1 in fp32 with each operation rounded to
-// nearest in a fixed order, and the saddle decider's centre value is formed in
-// fp32 the same way, so that these decisions are reproducible exactly.
+// nearest in a fixed order (within 5 u (|gx| + |gy|) of the exact value, u =
+// 2^-24, gx and gy its two terms), and the saddle decider's centre value
+// ((f0 + f1) + (f2 + f3)) / 4 is formed in fp32 the same way, so the results
+// are deterministic and differ from the exact marching squares only where a
+// corner or a saddle centre lies within that rounding of the isovalue.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -48,7 +51,6 @@ constexpr int kCI = 4;                   // rounds per tile
 constexpr int kIW = 31;                  // items per warp and round (lane 31 supplies the 32nd corner column)
 constexpr int kWin = 512;                // segment descriptors staged per warp and window
 constexpr int64_t kTile = (kCT / 32) * kCI * kIW;
-constexpr long long kWaitBudget3 = 4000000000ll;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr unsigned long long kAgg = 1ull << 62, kPre = 2ull << 62, kVal = (1ull << 62) - 1;
 
@@ -66,6 +68,7 @@ struct ContourParams {
     unsigned long long* count;
     unsigned long long* flags;  // [tiles] look-back words (zeroed before the launch)
     unsigned int* ticket;
+    long long budget;           // clock cycles before a look-back wait gives up
 };
 
 __device__ __forceinline__ unsigned long long ld_acq64(const unsigned long long* p) {
@@ -298,7 +301,7 @@ __global__ void __launch_bounds__(kCT) contour_kernel(const __grid_constant__ Co
                     const long long t0 = clock64();
                     fl = ld_acq64(p.flags + q);
                     while ((fl >> 62) == 0) {
-                        if (clock64() - t0 > kWaitBudget3) {
+                        if (clock64() - t0 > p.budget) {
                             atomicOr(&g_contour_status, 1u);
                             fl = kPre;
                             break;
@@ -411,10 +414,14 @@ lcp_status launch_contour(const ContourParams& p, const IsoParams& ip, int64_t t
     return LCP_OK;
 }
 
+// skip_first (the failure-path probe only): the ticket starts at 1, so tile 0
+// never runs and the grid has one block fewer.
 lcp_status run_contours(int mode, const ContourParams& p0, const float* iso, int K, void* ws, size_t ws_bytes,
-                        cudaStream_t st, const char* fn) {
+                        cudaStream_t st, const char* fn, bool skip_first = false) {
     ContourParams p = p0;
+    p.budget = wait_budget_cycles();
     const int64_t tiles = (p.n_items + kTile - 1) / kTile;
+    if (skip_first && tiles < 2) return fail(LCP_ERR_ARG, "%s: needs at least two tiles (%lld cells)", fn, (long long)kTile + 1);
     const size_t need = 256 + (size_t)std::max<int64_t>(tiles, 1) * 8;
     if (!ws || ((uintptr_t)ws & 255)) return fail(LCP_ERR_ARG, "%s: need a 256-byte aligned workspace", fn);
     if (ws_bytes < need) return fail(LCP_ERR_ARG, "%s: workspace too small (%zu < %zu bytes)", fn, ws_bytes, need);
@@ -422,6 +429,9 @@ lcp_status run_contours(int mode, const ContourParams& p0, const float* iso, int
     p.ticket = reinterpret_cast<unsigned int*>(ws);
     p.flags = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ws) + 256);
     if (cudaMemsetAsync(ws, 0, need, st) != cudaSuccess) return fail(LCP_ERR_CUDA, "%s: workspace clear failed", fn);
+    if (skip_first && cudaMemsetAsync(ws, 1, 1, st) != cudaSuccess)  // ticket = 1 (little-endian low byte)
+        return fail(LCP_ERR_CUDA, "%s: ticket set failed", fn);
+    const int64_t blocks = skip_first ? tiles - 1 : tiles;
     if (tiles == 0) {
         if (cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), st) != cudaSuccess)
             return fail(LCP_ERR_CUDA, "%s: count clear failed", fn);
@@ -435,13 +445,13 @@ lcp_status run_contours(int mode, const ContourParams& p0, const float* iso, int
     lcp_status s = LCP_OK;
     switch (mode) {
         case 0:
-            s = narrow ? launch_contour<0, uint32_t>(p, ip, tiles, st) : launch_contour<0, unsigned long long>(p, ip, tiles, st);
+            s = narrow ? launch_contour<0, uint32_t>(p, ip, blocks, st) : launch_contour<0, unsigned long long>(p, ip, blocks, st);
             break;
         case 1:
-            s = narrow ? launch_contour<1, uint32_t>(p, ip, tiles, st) : launch_contour<1, unsigned long long>(p, ip, tiles, st);
+            s = narrow ? launch_contour<1, uint32_t>(p, ip, blocks, st) : launch_contour<1, unsigned long long>(p, ip, blocks, st);
             break;
         default:
-            s = narrow ? launch_contour<2, uint32_t>(p, ip, tiles, st) : launch_contour<2, unsigned long long>(p, ip, tiles, st);
+            s = narrow ? launch_contour<2, uint32_t>(p, ip, blocks, st) : launch_contour<2, unsigned long long>(p, ip, blocks, st);
             break;
     }
     if (s != LCP_OK) return s;
@@ -482,10 +492,10 @@ extern "C" size_t lcp_contours_workspace_bytes(int M, int H, int W) {
     return 256 + (size_t)std::max<int64_t>((items + kTile - 1) / kTile, 1) * 8;
 }
 
-extern "C" lcp_status lcp_contours(const float* field, int H, int W, const float* iso, int K, float* seg, long long* key,
-                                   int64_t capacity, unsigned long long* count, void* workspace, size_t workspace_bytes,
-                                   lcp_stream_t stream) {
-    static const char* fn = "lcp_contours";
+namespace {
+lcp_status field_contours(const char* fn, bool skip_first, const float* field, int H, int W, const float* iso, int K,
+                          float* seg, long long* key, int64_t capacity, unsigned long long* count, void* workspace,
+                          size_t workspace_bytes, lcp_stream_t stream) {
     if (!field) return fail(LCP_ERR_ARG, "%s: NULL field", fn);
     if (H < 2 || W < 2) return fail(LCP_ERR_ARG, "%s: need H, W >= 2", fn);
     lcp_status s = check_contour_out(fn, H, W, iso, K, seg, capacity, count);
@@ -500,7 +510,22 @@ extern "C" lcp_status lcp_contours(const float* field, int H, int W, const float
     p.key = key;
     p.capacity = capacity;
     p.count = count;
-    return run_contours(0, p, iso, K, workspace, workspace_bytes, (cudaStream_t)stream, fn);
+    return run_contours(0, p, iso, K, workspace, workspace_bytes, (cudaStream_t)stream, fn, skip_first);
+}
+}  // namespace
+
+extern "C" lcp_status lcp_contours(const float* field, int H, int W, const float* iso, int K, float* seg, long long* key,
+                                   int64_t capacity, unsigned long long* count, void* workspace, size_t workspace_bytes,
+                                   lcp_stream_t stream) {
+    return field_contours("lcp_contours", false, field, H, W, iso, K, seg, key, capacity, count, workspace,
+                          workspace_bytes, stream);
+}
+
+extern "C" lcp_status lcp_test_stalled_lookback(const float* field, int H, int W, const float* iso, int K, float* seg,
+                                                long long* key, int64_t capacity, unsigned long long* count,
+                                                void* workspace, size_t workspace_bytes, lcp_stream_t stream) {
+    return field_contours("lcp_test_stalled_lookback", true, field, H, W, iso, K, seg, key, capacity, count, workspace,
+                          workspace_bytes, stream);
 }
 
 extern "C" lcp_status lcp_member_contours(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,

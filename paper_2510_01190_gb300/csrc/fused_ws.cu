@@ -54,7 +54,6 @@ constexpr int kRT = 256;           // LCP kernel threads = cell columns per tile
 constexpr int kTR = 8;             // cell rows per LCP tile
 constexpr int kMaxKPass = 32;      // isovalues per LCP launch
 constexpr size_t kL2Budget = 96ull << 20;  // workspace bytes a band may occupy (of the 129 MB L2)
-constexpr long long kWaitBudget = 4000000000ll;  // clock cycles (~2 s) before a dependency wait gives up
 
 // Statistics blocks [blo, bhi] of the statistics grid that cover the rows LCP
 // row band `by` needs (its vertex rows and one halo row each side).  The same
@@ -281,7 +280,46 @@ struct RowsParams {
     const uint32_t* dep;  // per row band: statistics blocks completed
     int64_t n_begin;      // statistics grid geometry, to recompute each band's requirement
     int sv;
+    long long budget;     // clock cycles before a dependency wait gives up
 };
+
+// Bounded wait (thread 0 of the block) until the statistics rows of LCP row
+// band `by` are complete; every thread returns whether the wait gave up.
+__device__ __forceinline__ bool wait_band(const RowsParams& p, int by) {
+    int gave_up = 0;
+    if (threadIdx.x == 0) {
+        int blo, bhi;
+        band_blocks(p.n_begin, p.sv, p.W, p.H, p.r_begin, p.r_end, by, blo, bhi);
+        const uint32_t need = (uint32_t)(bhi - blo + 1);
+        const long long t0 = clock64();
+        while (ld_acquire(&p.dep[by]) < need) {
+            if (clock64() - t0 > p.budget) {
+                atomicOr(&g_ws_status, 1u);
+                gave_up = 1;
+                break;
+            }
+            __nanosleep(200);
+        }
+    }
+    return __syncthreads_or(gave_up) != 0;
+}
+
+// After a wait that gave up, the band's records may be incomplete: this
+// thread's cell column gets NaN for every cell row [a, e) and isovalue of the
+// pass, and the mask word owner clears its words, so that no finite value is
+// ever computed from partial statistics.
+template <int KX, bool MASK, typename OutT>
+__device__ void fill_stalled(const RowsParams& p, int a, int e, int i, int wi, bool word_writer) {
+    const int Hc = p.H - 1, Wc = p.W - 1;
+    const int64_t plane = (int64_t)Hc * Wc, mplane = (int64_t)Hc * p.n_words;
+    OutT* o = reinterpret_cast<OutT*>(p.out);
+    const OutT nan = to_out<OutT>(__int_as_float(0x7FC00000));
+    for (int j = a; j < e; ++j)
+        for (int k = 0; k < KX; ++k) {
+            if (i < Wc) o[(int64_t)(p.kbase + k) * plane + (int64_t)j * Wc + i] = nan;
+            if (MASK && word_writer) p.mask[(int64_t)(p.kbase + k) * mplane + (int64_t)j * p.n_words + wi] = 0u;
+        }
+}
 
 // Records are read through L2 (ld.global.cg): the statistics grid may still be
 // writing other rows of the workspace, so no stale L1 line may be used.
@@ -320,21 +358,11 @@ __global__ void __launch_bounds__(kRT, KX <= 4 ? 3 : (KX <= 16 ? 2 : 1))
     const int a = p.r_begin + blockIdx.y * kTR;
     if (a >= p.r_end) return;
     const int e = min(a + kTR, p.r_end);  // cells [a, e), vertex rows a..e
-    if (p.dep) {  // wait (bounded) until the statistics rows this band reads are complete
-        if (t == 0) {
-            int blo, bhi;
-            band_blocks(p.n_begin, p.sv, W, H, p.r_begin, p.r_end, blockIdx.y, blo, bhi);
-            const uint32_t need = (uint32_t)(bhi - blo + 1);
-            const long long t0 = clock64();
-            while (ld_acquire(&p.dep[blockIdx.y]) < need) {
-                if (clock64() - t0 > kWaitBudget) {
-                    atomicOr(&g_ws_status, 1u);
-                    break;
-                }
-                __nanosleep(200);
-            }
-        }
-        __syncthreads();
+    // wait (bounded) until the statistics rows this band reads are complete
+    if (p.dep && wait_band(p, blockIdx.y)) {
+        const int wi0 = (c0 >> 5) + warp;
+        fill_stalled<KX, MASK, OutT>(p, a, e, c0 + t, wi0, lane == 0 && wi0 < p.n_words);
+        return;
     }
     // the next isovalue pass may launch once every block of this grid is past its wait
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -492,21 +520,10 @@ __global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer
     const int a = p.r_begin + blockIdx.y * kTR;
     if (a >= p.r_end) return;
     const int e = min(a + kTR, p.r_end);  // cells [a, e), vertex rows a..e
-    if (p.dep) {  // wait (bounded) until the statistics rows this band reads are complete
-        if (t == 0) {
-            int blo, bhi;
-            band_blocks(p.n_begin, p.sv, W, H, p.r_begin, p.r_end, blockIdx.y, blo, bhi);
-            const uint32_t need = (uint32_t)(bhi - blo + 1);
-            const long long t0 = clock64();
-            while (ld_acquire(&p.dep[blockIdx.y]) < need) {
-                if (clock64() - t0 > kWaitBudget) {
-                    atomicOr(&g_ws_status, 1u);
-                    break;
-                }
-                __nanosleep(200);
-            }
-        }
-        __syncthreads();
+    // wait (bounded) until the statistics rows this band reads are complete
+    if (p.dep && wait_band(p, blockIdx.y)) {
+        fill_stalled<KX, MASK, OutT>(p, a, e, c0w + lane, c0w >> 5, lane == 0 && (c0w >> 5) < p.n_words);
+        return;
     }
     // the next isovalue pass may launch once every block of this grid is past its wait
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -851,6 +868,7 @@ lcp_status run(const void* u, const void* v, int M, int H, int W, int64_t stride
         rp.dep = dep;
         rp.n_begin = sp.n_begin;
         rp.sv = kST * VEC;
+        rp.budget = wait_budget_cycles();
         s = out_dtype == LCP_F16 ? launch_rows<__half>(rp, iso, K, st) : launch_rows<float>(rp, iso, K, st);
         if (s != LCP_OK) return s;
     }
@@ -887,6 +905,7 @@ lcp_status ws_lcp_rows(const float4* rec, int64_t ps, int row0, int H, int W, in
     rp.dep = nullptr;  // records complete before this launch (stream order)
     rp.n_begin = 0;
     rp.sv = 1;
+    rp.budget = wait_budget_cycles();
     return out_dtype == LCP_F16 ? launch_rows<__half>(rp, iso, K, st, false) : launch_rows<float>(rp, iso, K, st, false);
 }
 
@@ -945,4 +964,44 @@ extern "C" lcp_status lcp_fused_ws(const void* u, const void* v, lcp_dtype in_dt
     const bool in8 = ((uintptr_t)u & 7) == 0 && ((uintptr_t)v & 7) == 0;
     return run<__nv_bfloat16, 4>(u, v, M, H, W, stride, ddof, dx, dy, iso, K, lcp_out, out_dtype, mask, workspace,
                                  workspace_bytes, in8 && stride % 4 == 0, st);
+}
+
+extern "C" lcp_status lcp_test_stalled_lcp_wait(int H, int W, const float* iso, int K, void* lcp_out,
+                                                lcp_dtype out_dtype, uint32_t* mask, void* workspace,
+                                                size_t workspace_bytes, lcp_stream_t stream) {
+    static const char* fn = "lcp_test_stalled_lcp_wait";
+    if (H < 2 || W < 2) return fail(LCP_ERR_ARG, "%s: need H, W >= 2", fn);
+    lcp_status s = check_iso(fn, iso, K);
+    if (s != LCP_OK) return s;
+    if (!lcp_out) return fail(LCP_ERR_ARG, "%s: NULL output", fn);
+    if (out_dtype != LCP_F32 && out_dtype != LCP_F16) return fail(LCP_ERR_ARG, "%s: out dtype must be F32 or F16", fn);
+    if ((uintptr_t)mask & 3) return fail(LCP_ERR_ARG, "%s: mask must be 4-byte aligned", fn);
+    if (!workspace || ((uintptr_t)workspace & 255)) return fail(LCP_ERR_ARG, "%s: need a 256-byte aligned workspace", fn);
+    const Layout L = layout(H, W, workspace_bytes);
+    if (workspace_bytes < L.total) return fail(LCP_ERR_ARG, "%s: workspace too small", fn);
+    if ((H - 1 + kTR - 1) / kTR > 65535) return fail(LCP_ERR_UNSUPPORTED, "%s: H too large", fn);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int r1 = min(L.band_rows, H - 1);
+    const int nby = (r1 + kTR - 1) / kTR;
+    uint32_t* dep = reinterpret_cast<uint32_t*>(workspace);
+    // counters at zero and no statistics grid to release them
+    if (cudaMemsetAsync(dep, 0, (size_t)nby * 4, st) != cudaSuccess) return fail(LCP_ERR_CUDA, "%s: counter reset failed", fn);
+    RowsParams rp;
+    rp.st = reinterpret_cast<float4*>(reinterpret_cast<char*>(workspace) + L.ctr_bytes);
+    rp.ps = (int64_t)(L.plane_bytes / sizeof(float4));
+    rp.row0 = 0;
+    rp.H = H;
+    rp.W = W;
+    rp.r_begin = 0;
+    rp.r_end = r1;
+    rp.sp = make_spacing(1.0, 1.0);
+    rp.out = lcp_out;
+    rp.mask = mask;
+    rp.n_words = (W - 1 + 31) / 32;
+    rp.kbase = 0;
+    rp.dep = dep;
+    rp.n_begin = 0;
+    rp.sv = kST * 4;
+    rp.budget = wait_budget_cycles();
+    return out_dtype == LCP_F16 ? launch_rows<__half>(rp, iso, K, st, false) : launch_rows<float>(rp, iso, K, st, false);
 }

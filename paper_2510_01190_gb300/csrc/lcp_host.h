@@ -45,6 +45,12 @@ lcp_status fused_tma(const void* u, const void* v, lcp_dtype in_dtype, int M, in
                      double dx, double dy, const float* iso, int K, void* out, lcp_dtype out_dtype, uint32_t* mask,
                      cudaStream_t st);
 
+// Clock-cycle budget of the bounded device waits that take it as a launch
+// parameter (the workspace path's waits for statistics rows, the contour
+// look-back): lcp_set_wait_budget's value, else the default (~2 s at 2 GHz).
+constexpr long long kDefaultWaitBudget = 4000000000ll;
+long long wait_budget_cycles();
+
 // Device status words of the kernels with bounded waits (one per translation
 // unit: device globals are not shared across units without relocatable code).
 uint32_t read_tma_status(bool reset);  // TMA row-march pipeline (mbarrier waits)

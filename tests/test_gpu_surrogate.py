@@ -5,8 +5,8 @@ Tolerances (BF16 operands, FP32 accumulation): the oracle evaluates the
 network with the same bf16-rounded weights and feature rows, so the remaining
 differences are the GPU's bf16 rounding of the hidden activations (relative
 2^-9) and the hardware tanh (relative ~2^-11); propagated through the 64-wide
-layers they stay below 1e-2 on the output and 3e-2 (relative, per tensor) on
-the gradients."""
+layers they stay below 1e-2 on the output; each gradient entry is compared
+with its own bound (test_backward_parity)."""
 
 import numpy as np
 import pytest
@@ -108,12 +108,34 @@ def test_backward_parity(lib):
     y, cache = S.mlp_forward(po, _np(feat)[:, :17], _np(prior))
     ref = S.mlp_backward(po, cache, t)
     got = G.mlp_unpack(_np(grad))
+    # element by element: every gradient entry is a sum over rows of a product
+    # of two per-row factors; the GPU rounds h1, dZ2 and dZ1 to bf16 (2^-9
+    # relative), evaluates tanh in hardware (~2^-11) and carries those errors
+    # through one more layer, so each product is within 2^-6 of the magnitude
+    # of its terms and a sum within 2^-6 of the sum of magnitudes
+    # (Sigma_r |a_r b_r| / n, the oracle's gradient of the same network with
+    # absolute values), plus 2^-9 of the tensor's largest magnitude for the
+    # saturated units whose tanh' = 1 - h^2 the rounding of h moves.
+    mag = _abs_gradient(po, cache, t)
     for k in ref:
-        a, b = np.asarray(got[k]).ravel(), np.asarray(ref[k]).ravel()
-        assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b) + 1e-9, k
+        a, b, m = (np.asarray(z, np.float64).ravel() for z in (got[k], ref[k], mag[k]))
+        tol = 2.0 ** -6 * m + 2.0 ** -9 * m.max() + 1e-12
+        assert np.all(np.abs(a - b) <= tol), (k, float(np.max(np.abs(a - b) / tol)))
     assert float(loss.item()) == pytest.approx(S.mse_loss(y, t), rel=1e-2)
     raw = _np(grad)
     assert np.all(raw[0:2048].reshape(64, 32)[:, 17:] == 0.0) and np.all(raw[6337:] == 0.0)
+
+
+def _abs_gradient(params, cache, t):
+    """Sigma over rows of |a_r b_r| / n for every gradient entry a^T b: the
+    chain rule of the oracle with every factor replaced by its magnitude."""
+    x, h1, h2, y = cache["x"], cache["h1"], cache["h2"], cache["y"]
+    n = x.shape[0]
+    dz3 = np.abs(2.0 * (y - np.asarray(t, np.float64)) / n * y * (1.0 - y))
+    dz2 = dz3[:, None] * np.abs(params["w3"])[None, :] * (1.0 - h2 * h2)
+    dz1 = (dz2 @ np.abs(params["W2"]).T) * (1.0 - h1 * h1)
+    return dict(W1=np.abs(x).T @ dz1, b1=dz1.sum(axis=0), W2=np.abs(h1).T @ dz2, b2=dz2.sum(axis=0),
+                w3=np.abs(h2).T @ dz3, b3=np.asarray(dz3.sum()))
 
 
 def test_backward_ragged_batch_equals_sum_of_parts(lib):
@@ -218,4 +240,4 @@ def test_trained_network_beats_the_closed_form_on_held_out_data(lib):
     rms_c, max_c = err(closed)
     rms_l, max_l = err(learned)
     assert rms_l < 0.9 * rms_c, (rms_l, rms_c)
-    assert max_l < 2.0 * max_c
+    assert max_l <= max_c, (max_l, max_c)

@@ -1,8 +1,12 @@
 """Pins of the visual-output oracle (CPU only).
 
-Colour map (reading R17): exact integer byte formulas on dyadic inputs (where
-every fp32 step is exact), the stops' own colours, interpolation midpoints
-worked by hand, clamping and special values, and monotonicity."""
+Colour map (reading R17): exact integer byte formulas on dyadic inputs, the
+stops' own colours, interpolation midpoints worked by hand, rational
+arithmetic for the levels, clamping and special values, and monotonicity.
+Marching squares (reading R18): all 16 cell cases by hand, the saddle decided
+by the exact centre value, linear fields (endpoints on the level line),
+agreement with the crossing mask, closed loops, NaN cells, and spaghetti
+contours of linear members."""
 
 import math
 
@@ -79,11 +83,30 @@ def test_monotone_channel_is_non_decreasing():
     assert got[0, 0] == 0 and got[-1, 0] == 255
 
 
-def test_overflowing_range_maps_infinities_like_maxnum():
-    """vmax - vmin overflows to inf, so R = 0 and x = +inf gives inf * 0 = NaN;
-    maxNum turns it into 0, so +inf takes the first stop's colour."""
-    got = V.colormap_rgba(np.array([np.inf, 1.0]), -3e38, 3e38, GREY)
-    assert list(got[0]) == [0, 0, 0, 0] and list(got[1]) == [0, 0, 0, 0]
+def test_range_beyond_fp32_is_plain_arithmetic_in_fp64():
+    """The map is a statement about real numbers: a range wider than fp32 can
+    hold still maps its midpoint to the middle of a grey ramp, +inf to the top
+    and -inf to the bottom."""
+    got = V.colormap_rgba(np.array([np.inf, 0.0, -np.inf]), -3e38, 3e38, GREY)
+    assert list(got[0]) == [255] * 4 and list(got[1]) == [128] * 4 and list(got[2]) == [0] * 4
+
+
+def test_levels_are_the_exact_affine_interpolant():
+    """255 ch + 1/2 inside a segment is affine in x with the slope fixed by the
+    stop table and the range: check it against rationals."""
+    from fractions import Fraction as Fr
+    stops = [(0.0, 0.0, 0.25, 0.5, 1.0), (0.3, 0.7, 0.1, 0.9, 0.0), (1.0, 1.0, 1.0, 0.0, 0.5)]
+    xs = [-0.7, -0.2, 0.1, 0.35, 0.9]
+    y, s = V.colormap_levels(np.array(xs), -0.5, 1.0, stops)
+    for n, x in enumerate(xs):
+        t = min(max((Fr(x) - Fr(-0.5)) / (Fr(1.0) - Fr(-0.5)), Fr(0)), Fr(1))
+        q = 1 if t >= Fr(0.3) else 0
+        assert s[n] == q
+        a, b = stops[q], stops[q + 1]
+        f = (t - Fr(a[0])) / (Fr(b[0]) - Fr(a[0]))
+        for ch in range(4):
+            want = 255 * (Fr(a[1 + ch]) + f * (Fr(b[1 + ch]) - Fr(a[1 + ch]))) + Fr(1, 2)
+            assert abs(y[n, ch] - float(want)) <= 1e-12
 
 
 # ---------------------------------------------------------------------------
@@ -172,18 +195,24 @@ def test_nan_corner_cells_give_no_segments():
     assert keys.size == 0
 
 
-def test_member_divergence32_fixed_fp32_order():
-    g = np.random.Generator(np.random.PCG64(23))
-    u = g.normal(0, 1, (3, 6, 7)).astype(np.float32)
-    v = g.normal(0, 1, (3, 6, 7)).astype(np.float32)
-    d = V.member_divergence32(u, v, 0.5, 2.0)
-    assert d.dtype == np.float32
-    ref = O.divergence_of_field(u, v, 0.5, 2.0)
-    assert np.max(np.abs(d - ref)) <= 4 * 2.0 ** -24 * np.max(np.abs(ref)) * 8
-    # dyadic members: every fp32 step is exact
-    ud = (g.integers(-64, 64, (2, 5, 6)) / 8.0).astype(np.float32)
-    vd = (g.integers(-64, 64, (2, 5, 6)) / 8.0).astype(np.float32)
-    assert np.array_equal(V.member_divergence32(ud, vd, 0.5, 0.25), O.divergence_of_field(ud, vd, 0.5, 0.25))
+def test_saddle_pairing_follows_the_exact_centre_value():
+    """A saddle whose corners sum to a tiny positive number: the centre
+    (f0 + f1 + f2 + f3) / 4 = 2^-42 lies above c = 0 (not below), so the
+    below corners v0 and v2 are cut off separately: (E0, E3) and (E1, E2).
+    With the sign flipped the centre is below, on v0's side, and the
+    segments are (E0, E1) and (E2, E3).  A fp32 centre ((f0 + f1) + (f2 + f3))
+    * 0.25 would round both to 0 and take the first pairing twice."""
+    tiny = 2.0 ** -40
+    f = np.array([[-1.0, 1.0 + tiny], [1.0, -1.0]])  # v0 = -1, v1 = 1 + tiny, v3 = 1, v2 = -1
+    keys, segs = V.marching_squares(f, [0.0])
+    assert list(keys) == [0, 1]
+    # v0 below, centre not below (v0's side is "below"): pairs (E0, E3) and (E1, E2)
+    assert segs[0][1] == 0.0 and segs[0][2] == 0.0      # E0 then E3
+    assert segs[1][0] == 1.0 and segs[1][3] == 1.0      # E1 then E2
+    f2 = np.array([[-1.0 - tiny, 1.0], [1.0, -1.0]])     # centre -2^-42: below, v0's side
+    keys, segs = V.marching_squares(f2, [0.0])
+    assert segs[0][1] == 0.0 and segs[0][2] == 1.0      # E0 then E1
+    assert segs[1][1] == 1.0 and segs[1][2] == 0.0      # E2 then E3
 
 
 def test_spaghetti_keys_offset_by_member():
@@ -192,9 +221,33 @@ def test_spaghetti_keys_offset_by_member():
     v = g.normal(0, 1, (4, 9, 8)).astype(np.float32)
     keys, segs = V.spaghetti_contours(u, v, 1.0, 1.0, [0.0, 0.4])
     per = 8 * 7 * 2 * 2
-    d = V.member_divergence32(u, v, 1.0, 1.0)
+    d = O.divergence_of_field(u, v, 1.0, 1.0)
     for m in range(4):
         sel = (keys // per) == m
         k_m, s_m = V.marching_squares(d[m], [0.0, 0.4])
         assert np.array_equal(keys[sel] - m * per, k_m) and np.array_equal(segs[sel], s_m)
     assert np.all(np.diff(keys) > 0)
+
+
+def test_spaghetti_of_a_linear_member_lies_on_its_level_line():
+    """Eq. 1 is exact on linear members (u = a x, v = b y gives divergence
+    a/dx' + b/dy' per unit index), so every endpoint of a member's contour at c
+    lies where that member's divergence plane equals c."""
+    h, w = 12, 15
+    y, x = np.mgrid[0:h, 0:w].astype(np.float64)
+    u = np.stack([0.3 * x * x, -0.2 * x * x])            # divergence 0.6 x / dx (central), -0.4 x / dx
+    v = np.stack([0.1 * y * y, 0.5 * y * y])
+    dx, dy = 0.5, 2.0
+    keys, segs = V.spaghetti_contours(u, v, dx, dy, [1.5])
+    d = O.divergence_of_field(u, v, dx, dy)
+    per = (h - 1) * (w - 1) * 2
+    for k, s in zip(keys, segs):
+        m = k // per
+        for px, py in ((s[0], s[1]), (s[2], s[3])):
+            # bilinear interpolation of the member's divergence at the endpoint equals c on an edge
+            i0, j0 = min(int(np.floor(px)), w - 2), min(int(np.floor(py)), h - 2)
+            fx, fy = px - i0, py - j0
+            val = ((1 - fx) * (1 - fy) * d[m, j0, i0] + fx * (1 - fy) * d[m, j0, i0 + 1]
+                   + (1 - fx) * fy * d[m, j0 + 1, i0] + fx * fy * d[m, j0 + 1, i0 + 1])
+            assert abs(val - 1.5) < 1e-9
+    assert keys.size > 10

@@ -49,8 +49,26 @@ def test_static_scratch_matches_workspace_path_twice(lib, h, w, m, k, dt):
         torch.cuda.synchronize()
         err = (out - ref).abs().max().item()
         assert err <= LCP_TOL, err
+        # the same kernels on the same per-vertex records: identical bits, whatever the bands
+        assert torch.equal(out, ref)
         assert torch.equal(mask, ref_mask)
     assert lib.lcp_device_status(reset=True) == 0
+
+
+def test_static_scratch_bands_differ_from_the_workspace_layout():
+    """The 600 x 8192 case really runs other bands than lcp_fused_ws with its
+    full workspace: 248 rows in the 64 MiB scratch against 376 (host arithmetic
+    of the library; no GPU needed)."""
+    from paper_2510_01190_gb300 import _binding
+
+    try:
+        clib = _binding.load()
+    except RuntimeError as e:
+        pytest.skip(f"library not buildable here: {e}")
+    full = clib.lcp_fused_workspace_bytes(3, 600, 8192, 0)
+    assert clib.lcp_fused_band_rows(600, 8192, full) == 376
+    assert clib.lcp_fused_band_rows(600, 8192, 64 << 20) == 248
+    assert clib.lcp_fused_band_rows(721, 1440, 64 << 20) == 720  # one band
 
 
 @pytest.mark.gpu
