@@ -17,6 +17,7 @@ on the same workload, a bounded row band per step, on the host cores.
 from __future__ import annotations
 
 import argparse
+import math
 import hashlib
 import json
 import os
@@ -43,8 +44,8 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-mc", action="store_true", help="skip the Monte Carlo equal-error comparison")
@@ -312,34 +313,10 @@ def our_arm(args):
     def step():
         lib.lcp_fused_ws(u, v, iso, 1.0, 1.0, 1, mask=True, out=out, mask_out=mask)
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-
-    clocks = ClockSampler(local).start()
-    time.sleep(0.35)  # let the sampler start
     n = args.steps
-    # two events on the launching stream bracket the K steps (a pair per step
-    # would put a timestamp write between every two steps)
-    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if pg:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    t_wall0 = time.time()
-    e_start.record(stream)
-    for _ in range(n):
-        step()
-    e_end.record(stream)
-    torch.cuda.synchronize()
-    t_wall1 = time.time()
-    if pg:
-        torch.distributed.barrier()
-    time.sleep(0.25)
-    clocks.stop()
-    total_ms = e_start.elapsed_time(e_end)
-    kern_ms = total_ms / n  # this rank's mean step (both kernels and the counter reset)
-    total_ms = max_over_ranks(total_ms, device=dev)
-    ms_per_step = total_ms / n
+    block_ms, blk, clk = timed_blocks(torch, step, n, args.warmup, local, pg, dev)
+    kern_ms = blk["block_ms_median"] / n  # this rank's median step (both kernels and the counter reset)
+    ms_per_step = block_ms / n  # max over ranks
     value = weak_scaling_value(Hc * Wc, world, ms_per_step)
 
     # algorithmic bytes of one launch: members read once + LCP map + mask written once
@@ -383,7 +360,6 @@ def our_arm(args):
         cpu = cpu_baseline(d)
 
     if rank == 0:
-        clk = clocks.summary(t_wall0, t_wall1)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -391,9 +367,10 @@ def our_arm(args):
             "config": {"workload": WORKLOAD, "H": H, "W": W, "M": M, "K": K, "global_batch": world,
                        "parallelism": f"independent fields x{world}" if world > 1 else "single",
                        "l2": "no flush: inputs 424 MB > 129 MB L2",
+                       "timing": blk,
                        "lcp_values_per_s": value * K, "hbm_frac_of_measured": roof["frac"]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "vs_mc": vs_mc,
-            "clocks": clk, "gpu_launches": 2 * n,  # statistics + LCP kernel per step (the counter reset is a memset)
+            "clocks": clk, "gpu_launches": 2 * n * blk["blocks"],  # statistics + LCP kernel per step, every block
             "gpu": torch.cuda.get_device_name(dev),
         }
         print(json.dumps(line), flush=True)
@@ -911,6 +888,51 @@ def timed_steps(torch, step, n, warmup, local, pg, dev):
     total_ms = max_over_ranks(ev[0][0].elapsed_time(ev[-1][1]), device=dev)
     kern_ms = sum(a.elapsed_time(b) for a, b in ev) / n
     return total_ms, kern_ms, clocks.summary(t0, t1)
+
+
+def timed_blocks(torch, step, k, warmup, local, pg, dev, min_seconds=0.5, max_blocks=400):
+    """W warm-up steps, then blocks of exactly k steps back to back, each
+    bracketed by a pair of CUDA events on the launching stream (one pair per
+    block, not per step, so no timestamp write sits between two steps), enough
+    blocks to fill ~min_seconds so that the clock sampler sees the timed region.
+    A barrier and a device synchronisation bracket the whole timed region.
+    Returns (median block ms, max over ranks; block statistics; clocks summary)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(max(warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):  # one untimed block sizes the timed region
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    est = max(e0.elapsed_time(e1), 1e-3)
+    blocks = int(min(max_blocks, max(5, math.ceil(min_seconds * 1e3 / est))))
+    clocks = ClockSampler(local).start()
+    time.sleep(0.35)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(blocks + 1)]
+    if pg:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    evs[0].record(stream)
+    for b in range(blocks):
+        for _ in range(k):
+            step()
+        evs[b + 1].record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if pg:
+        torch.distributed.barrier()
+    time.sleep(0.25)
+    clocks.stop()
+    per = sorted(evs[b].elapsed_time(evs[b + 1]) for b in range(blocks))
+    med = float(np.median(per))
+    stats = {"blocks": blocks, "steps_per_block": k, "block_ms_median": round(med, 5),
+             "block_ms_min": round(per[0], 5), "block_ms_max": round(per[-1], 5),
+             "timed_region_s": round(t1 - t0, 3)}
+    return max_over_ranks(med, device=dev), stats, clocks.summary(t0, t1)
 
 
 def _finish(torch, pg, line, rank):
