@@ -503,8 +503,9 @@ __global__ void __launch_bounds__(kRT, KX <= 4 ? 3 : (KX <= 16 ? 2 : 1))
 // Barrier-free variant: every warp evaluates 32 cells on its own.  Lane l owns
 // vertex c0w + l; the right neighbour's (P(D<c), P(D>=c)) and class bits come
 // from lane l + 1 by shuffle, and for lane 31 from the warp's 33rd vertex,
-// whose isovalues are evaluated one per lane (lane k: isovalue k) and passed
-// on by shuffle.  No shared memory, no barriers after the dependency wait;
+// whose four stencil records are loaded one per lane 0..3 and shared by
+// shuffle, and whose isovalues are evaluated one per lane (lane k: isovalue
+// k) and passed on by shuffle.  No shared memory, no barriers after the dependency wait;
 // 32-cell warps keep the mask words aligned.  KX <= 8 isovalues per pass.
 constexpr int kWT = 128;  // threads (4 warps = 128 cells) per block
 
@@ -534,7 +535,7 @@ __global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer
     const float sx = osx ? p.sp.sx1 : p.sp.sx2, sxq = osx ? p.sp.sx1q : p.sp.sx2q;
     const bool edge_lane = lane == 0 || lane == 31;
     const int iedge = lane == 0 ? max(ic - 1, 0) : min(ic + 1, W - 1);
-    const int ix = min(c0w + 32, W - 1);  // the warp's 33rd vertex (lane 0 loads its records)
+    const int ix = min(c0w + 32, W - 1);  // the warp's 33rd vertex
     const bool osxx = ix == 0 || ix == W - 1;
     const float sx_x = osxx ? p.sp.sx1 : p.sp.sx2, sxq_x = osxx ? p.sp.sx1q : p.sp.sx2q;
     const int ixl = max(ix - 1, 0), ixr = min(ix + 1, W - 1);
@@ -547,20 +548,30 @@ __global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer
     for (int k = 0; k < KX; ++k)
         if (k == lane) cl = c[k];
 
-    const float4* up = p.st + (int64_t)(a - p.row0) * W;  // u records of the current row
-    const float4* vpl = p.st + p.ps;
-    auto vrow = [&](int j) { return vpl + (int64_t)(j - p.row0) * W; };
-    float4 U = ld_rec(up + ic), UE = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (edge_lane) UE = ld_rec(up + iedge);
-    float4 VM = ld_rec(vrow(max(a - 1, 0)) + ic), V0 = ld_rec(vrow(a) + ic), VP = ld_rec(vrow(min(a + 1, H - 1)) + ic);
-    // 33rd vertex records (lane 0): u at ix-1, ix+1; v at (j-1, ix), (j+1, ix)
-    float4 XL = make_float4(0.f, 0.f, 0.f, 0.f), XR = XL, XD = XL, XU = XL;
-    if (lane == 0) {
-        XL = ld_rec(up + ixl);
-        XR = ld_rec(up + ixr);
-        XD = ld_rec(vrow(max(a - 1, 0)) + ix);
-        XU = ld_rec(vrow(min(a + 1, H - 1)) + ix);
-    }
+    const float4* ubase = p.st - (int64_t)p.row0 * W;  // u records of grid row j at ubase + j W
+    const float4* vbase = ubase + p.ps;
+    auto urow = [&](int j) { return ubase + (int64_t)j * W; };
+    auto vrow = [&](int j) { return vbase + (int64_t)j * W; };
+    // the records one vertex row needs beyond the sliding v window: own u, the warp-edge u neighbour,
+    // the v record two rows down (the window's next VP), and one record of the 33rd vertex's stencil
+    // per lane 0..3 (u at ix-1, u at ix+1, v at (j-1, ix), v at (j+1, ix))
+    struct RowRec {
+        float4 U, UE, VN, X;
+    };
+    auto load_row = [&](int j) {
+        RowRec r;
+        r.U = ld_rec(urow(j) + ic);
+        r.UE = edge_lane ? ld_rec(urow(j) + iedge) : make_float4(0.f, 0.f, 0.f, 0.f);
+        r.VN = ld_rec(vrow(min(j + 1, H - 1)) + ic);
+        r.X = lane == 0 ? ld_rec(urow(j) + ixl)
+                        : lane == 1 ? ld_rec(urow(j) + ixr)
+                                    : lane == 2 ? ld_rec(vrow(max(j - 1, 0)) + ix)
+                                                : lane == 3 ? ld_rec(vrow(min(j + 1, H - 1)) + ix)
+                                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        return r;
+    };
+    float4 VM = ld_rec(vrow(max(a - 1, 0)) + ic), V0 = ld_rec(vrow(a) + ic);
+    RowRec R0 = load_row(a);  // row j (its VN is v at j + 1)
     float ph_prev[KX], qh_prev[KX];
     uint32_t b_prev = 0, bn_prev = 0;
     const Off plane = (Off)Hc * (Off)Wc, mplane = (Off)Hc * (Off)p.n_words;
@@ -571,44 +582,29 @@ __global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer
     for (int jj = 0; jj <= kTR; ++jj) {  // vertex rows a .. e (at most kTR + 1), unrolled: no window moves
         const int j = a + jj;
         if (j > e) break;
-        const float4 Uc = U, UEc = UE, XLc = XL, XRc = XR, XDc = XD, XUc = XU;
-        float4 Vn = VP;
-        if (j < e) {  // next row in flight while this one is evaluated
-            up += W;
-            U = ld_rec(up + ic);
-            if (edge_lane) UE = ld_rec(up + iedge);
-            Vn = ld_rec(vrow(min(j + 2, H - 1)) + ic);
-            if (lane == 0) {
-                XL = ld_rec(up + ixl);
-                XR = ld_rec(up + ixr);
-                XD = ld_rec(vrow(j) + ix);
-                XU = ld_rec(vrow(min(j + 2, H - 1)) + ix);
-            }
-        }
+        const RowRec C = R0;
+        const float4 VP = C.VN;
+        if (j < e) R0 = load_row(j + 1);  // the next row in flight while this one is evaluated
         const bool osy = j == 0 || j == H - 1;
         const float sy = osy ? p.sp.sy1 : p.sp.sy2, syq = osy ? p.sp.sy1q : p.sp.sy2q;
         // own vertex (Eqs. 2/3, one-sided at the edges)
-        float4 L = make_float4(__shfl_up_sync(0xFFFFFFFFu, Uc.x, 1), __shfl_up_sync(0xFFFFFFFFu, Uc.y, 1),
-                               __shfl_up_sync(0xFFFFFFFFu, Uc.z, 1), 0.f);
-        float4 R = make_float4(__shfl_down_sync(0xFFFFFFFFu, Uc.x, 1), __shfl_down_sync(0xFFFFFFFFu, Uc.y, 1),
-                               __shfl_down_sync(0xFFFFFFFFu, Uc.z, 1), 0.f);
-        if (lane == 0) L = UEc;
-        if (lane == 31) R = UEc;
-        if (ic == 0) L = Uc;
-        if (ic == W - 1) R = Uc;
+        float4 L = make_float4(__shfl_up_sync(0xFFFFFFFFu, C.U.x, 1), __shfl_up_sync(0xFFFFFFFFu, C.U.y, 1),
+                               __shfl_up_sync(0xFFFFFFFFu, C.U.z, 1), 0.f);
+        float4 R = make_float4(__shfl_down_sync(0xFFFFFFFFu, C.U.x, 1), __shfl_down_sync(0xFFFFFFFFu, C.U.y, 1),
+                               __shfl_down_sync(0xFFFFFFFFu, C.U.z, 1), 0.f);
+        if (lane == 0) L = C.UE;
+        if (lane == 31) R = C.UE;
+        if (ic == 0) L = C.U;
+        if (ic == W - 1) R = C.U;
         const float4 Vlo = j > 0 ? VM : V0;
         const float4 Vhi = j < H - 1 ? VP : V0;
         const float mu = fmaf((R.x - L.x) + (R.y - L.y), sx, ((Vhi.x - Vlo.x) + (Vhi.y - Vlo.y)) * sy);
         const float var = fmaf(R.z + L.z, sxq, (Vhi.z + Vlo.z) * syq);
-        // 33rd vertex on lane 0, then to every lane
-        float mux = 0.f, varx = 0.f;
-        if (lane == 0) {
-            // (ixl, ixr) and the clamped rows already are the one-sided stencil at the edges
-            mux = fmaf((XRc.x - XLc.x) + (XRc.y - XLc.y), sx_x, ((XUc.x - XDc.x) + (XUc.y - XDc.y)) * sy);
-            varx = fmaf(XRc.z + XLc.z, sxq_x, (XUc.z + XDc.z) * syq);
-        }
-        mux = __shfl_sync(0xFFFFFFFFu, mux, 0);
-        varx = __shfl_sync(0xFFFFFFFFu, varx, 0);
+        // the 33rd vertex (every lane, from lanes 0..3's records); (ixl, ixr) and the clamped rows
+        // already are the one-sided stencil at the edges
+        const float4 XLc = shfl_rec(C.X, 0), XRc = shfl_rec(C.X, 1), XDc = shfl_rec(C.X, 2), XUc = shfl_rec(C.X, 3);
+        const float mux = fmaf((XRc.x - XLc.x) + (XRc.y - XLc.y), sx_x, ((XUc.x - XDc.x) + (XUc.y - XDc.y)) * sy);
+        const float varx = fmaf(XRc.z + XLc.z, sxq_x, (XUc.z + XDc.z) * syq);
         const bool zero = var == 0.0f;
         const float s = rsqrtf(2.0f * var);
         float2 pq[KX];
@@ -656,7 +652,6 @@ __global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer
         bn_prev = bn;
         VM = V0;
         V0 = VP;
-        VP = Vn;
     }
 }
 
