@@ -658,6 +658,40 @@ lcp_status lcp_colormap(const float* values, int planes, int rows, int cols, flo
 lcp_status lcp_philox_fill(uint64_t seed, uint32_t c1, uint64_t offset, int64_t count,
                            uint32_t* out, lcp_stream_t stream);
 
+/*
+ * Multi-GPU partition (host arithmetic; no device work, no allocation).
+ *
+ * The LCP of a cell depends only on its four vertices' statistics and their
+ * stencil neighbours (Eqs. 2/3; the paper's per-pixel data parallelism,
+ * Sec. 3.3), so one field splits over ranks into strips of cell rows that need
+ * no exchange: each rank re-reads a halo of member rows.
+ *
+ * lcp_strip_plan - rank `rank` of `nranks` (0 <= rank < nranks) takes the cell
+ * rows [cell_begin, cell_end) = [floor(rank (H-1) / nranks), floor((rank+1)
+ * (H-1) / nranks)); to compute them it reads the vertex rows [vrow_begin,
+ * vrow_end) = [max(cell_begin - 1, 0), min(cell_end + 2, H)) of every member
+ * and evaluates them as a grid of their own (same W, member_stride and
+ * spacing, u and v advanced by vrow_begin * W elements).  Of that sub-grid's
+ * cell rows it keeps [cell_begin - vrow_begin, cell_end - vrow_begin): the
+ * others sit next to a halo row whose one-sided difference is not the full
+ * grid's.  The kept rows equal the whole-grid result exactly.  More ranks
+ * than cell rows leave some strips empty (vrow_begin == vrow_end).  Errors:
+ * LCP_ERR_ARG for H < 2, a rank outside [0, nranks) or NULL outputs.
+ */
+lcp_status lcp_strip_plan(int H, int nranks, int rank, int* vrow_begin, int* vrow_end, int* cell_begin,
+                          int* cell_end);
+
+/*
+ * lcp_lpt_assign - whole fields of a batch to ranks by the
+ * longest-processing-time rule: fields in decreasing cost (ties in index
+ * order), each to the currently least-loaded rank (ties to the lowest rank),
+ * so that every rank computes the same plan.  cost: n host int64 >= 0 (e.g.
+ * member bytes); owner: n host ints receive the rank of each field; load
+ * (nranks host int64, may be NULL) receives each rank's total.  The largest
+ * load is at most (4/3 - 1/(3 nranks)) of the best possible (Graham, 1969).
+ */
+lcp_status lcp_lpt_assign(const int64_t* cost, int n, int nranks, int* owner, int64_t* load);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,9 @@ __all__ = [
     "lcp_set_wait_budget",
     "lcp_test_stalled_lcp_wait",
     "lcp_test_stalled_lookback",
+    "lcp_strip_plan",
+    "lcp_lpt_assign",
+    "lcp_fused_strip",
     "mask_words_per_row",
     "unpack_mask",
     "LCP_F32",
@@ -142,6 +145,8 @@ _SIGNATURES = {
     "lcp_fused_static_ws": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double, c_fp,
                                     c_int, c_vp, c_int, c_vp, c_vp]),
     "lcp_set_wait_budget": (ctypes.c_longlong, [ctypes.c_longlong]),
+    "lcp_strip_plan": (c_int, [c_int, c_int, c_int] + [ctypes.POINTER(c_int)] * 4),
+    "lcp_lpt_assign": (c_int, [ctypes.POINTER(c_i64), c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_i64)]),
     "lcp_test_stalled_lcp_wait": (c_int, [c_int, c_int, c_fp, c_int, c_vp, c_int, c_vp, c_vp, ctypes.c_size_t, c_vp]),
     "lcp_test_stalled_lookback": (c_int, [c_vp, c_int, c_int, c_fp, c_int, c_vp, c_vp, c_i64, c_vp, c_vp,
                                           ctypes.c_size_t, c_vp]),
@@ -666,6 +671,44 @@ def lcp_test_stalled_lookback(field, isovalues, capacity: int):
                                                 _stream())
 
     return _contour_call(launch, 1, h, w, k, field.device, capacity, True, None)
+
+
+def lcp_strip_plan(h: int, nranks: int, rank: int):
+    """Row strip of one rank (host arithmetic, no GPU needed): returns
+    (vrow_begin, vrow_end, cell_begin, cell_end); the rank evaluates vertex rows
+    [vrow_begin, vrow_end) as a grid of their own and keeps its cell rows
+    [cell_begin - vrow_begin, cell_end - vrow_begin)."""
+    out = [c_int(0) for _ in range(4)]
+    _check(load(build_if_stale=False).lcp_strip_plan(int(h), int(nranks), int(rank), *[ctypes.byref(o) for o in out]))
+    return tuple(int(o.value) for o in out)
+
+
+def lcp_lpt_assign(costs, nranks: int):
+    """Whole fields to ranks, largest first to the least-loaded rank (host
+    arithmetic): returns (owner list, per-rank load list)."""
+    n = len(costs)
+    c = (c_i64 * max(n, 1))(*[int(x) for x in costs])
+    owner = (c_int * max(n, 1))()
+    ld = (c_i64 * nranks)()
+    _check(load(build_if_stale=False).lcp_lpt_assign(c, n, int(nranks), owner, ld))
+    return [int(owner[i]) for i in range(n)], [int(ld[r]) for r in range(nranks)]
+
+
+def lcp_fused_strip(u, v, isovalues, nranks: int, rank: int, dx: float = 1.0, dy: float = 1.0, ddof: int = 1,
+                    mask: bool = False):
+    """This rank's strip of the LCP map of the field (u, v) [M, H, W]: the
+    kept cell rows [cell_begin, cell_end) of lcp_fused_ws run on the strip's
+    vertex rows (a view: no copy).  Returns (cell_begin, lcp [K, rows, W-1],
+    mask words or None)."""
+    m, h, w, stride = _members(u, v)
+    vb, ve, cb, ce = lcp_strip_plan(h, nranks, rank)
+    k = len(_iso(isovalues)[0])
+    if cb == ce:
+        empty = torch.empty((k, 0, w - 1), dtype=torch.float32, device=u.device)
+        return cb, empty, (torch.empty((k, 0, mask_words_per_row(w)), dtype=torch.int32, device=u.device) if mask else None)
+    lcp, words = lcp_fused_ws(u[:, vb:ve], v[:, vb:ve], isovalues, dx, dy, ddof, mask=mask)
+    keep = slice(cb - vb, ce - vb)
+    return cb, lcp[:, keep], (words[:, keep] if mask else None)
 
 
 def lcp_batch_workspace_bytes(n_fields: int, n_iso: int) -> int:

@@ -460,3 +460,17 @@ def test_fused_host_pinned_in_place_and_pageable_staged(lib, dtype):
             torch.cuda.synchronize()
             assert none is None and torch.equal(out2, ref)
     assert lib.lcp_device_status(reset=True) == 0
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7])
+def test_row_strips_reassemble_the_whole_map(lib, n):
+    """The multi-GPU partition run on one GPU: every strip's kept rows of
+    lcp_fused_ws on its vertex rows (with the halo) equal the whole-grid map and
+    mask bit for bit (the same per-vertex records and stencils)."""
+    d = synth.fourier_ensemble(9, h=203, w=311, m=7, k=3)
+    u, v, iso = _dev(d["u"]), _dev(d["v"]), d["isovalues"]
+    whole, wmask = lib.lcp_fused_ws(u, v, iso, mask=True)
+    parts = [lib.lcp_fused_strip(u, v, iso, n, r, mask=True) for r in range(n)]
+    assert [p[0] for p in parts] == [lib.lcp_strip_plan(203, n, r)[2] for r in range(n)]
+    assert torch.equal(torch.cat([p[1] for p in parts], dim=1), whole)
+    assert torch.equal(torch.cat([p[2] for p in parts], dim=1), wmask)
