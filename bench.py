@@ -192,6 +192,27 @@ def profiled_traffic(profile="lcp_fused_ws_latlon_721x1440_m51_k8.md", sources=(
 
 
 # ---------------------------------------------------------------------------
+def crop_accuracy(lcp, get_crop, H, W, iso, crops, dx=1.0, dy=1.0):
+    """Max |GPU - FP64 oracle| of the LCP on crops of the field.  Each crop
+    (r0, r1, c0, c1) of vertices is evaluated by the oracle as a grid of its
+    own; cell rows and columns next to a crop edge that is not a grid edge
+    are dropped (their stencils reach outside the crop).  get_crop(r0, r1, c0,
+    c1) returns fp32 numpy (u, v) [M, r1-r0, c1-c0]."""
+    import oracle as O
+
+    worst, cells = 0.0, 0
+    for (r0, r1, c0, c1) in crops:
+        u, v = get_crop(r0, r1, c0, c1)
+        ref = O.lcp_closed_form(u, v, dx, dy, iso)["lcp"]
+        a, b = (1 if r0 > 0 else 0), ref.shape[1] - (1 if r1 < H else 0)
+        cA, cB = (1 if c0 > 0 else 0), ref.shape[2] - (1 if c1 < W else 0)
+        got = lcp[:, r0 + a:r0 + b, c0 + cA:c0 + cB].float().cpu().numpy()
+        worst = max(worst, float(np.max(np.abs(got - ref[:, a:b, cA:cB]))))
+        cells += got.shape[1] * got.shape[2]
+    return {"max_abs_err_vs_fp64_oracle": worst, "cells_checked": cells, "isovalues": len(iso),
+            "crops": [list(c) for c in crops]}
+
+
 def make_workload():
     from paper_2510_01190_gb300 import synth
 
@@ -367,6 +388,11 @@ def our_arm(args):
                "h2d_mode": "pinned members read in place by the statistics kernel over the CPU-GPU link",
                "api": "lcp_fused_host (pinned host members in, pinned LCP map and mask words out)"}
 
+    accuracy = None
+    if rank == 0 and not strips:  # the map of the last timed step, against the oracle on three crops
+        accuracy = crop_accuracy(out, lambda r0, r1, c0, c1: (d["u"][:, r0:r1, c0:c1], d["v"][:, r0:r1, c0:c1]),
+                                 H, W, iso, [(0, 24, 0, W), (350, 374, 0, W), (H - 24, H, 0, W)])
+
     vs_mc = None
     if not args.no_mc and rank == 0:
         vs_mc = mc_equal_error(lib, torch, u, v, iso, kern_ms / 1e3)
@@ -386,7 +412,7 @@ def our_arm(args):
                        "l2": "no flush: inputs 424 MB > 129 MB L2",
                        "timing": blk,
                        "lcp_values_per_s": value * K, "hbm_frac_of_measured": roof["frac"]},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "vs_mc": vs_mc,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "vs_mc": vs_mc, "accuracy": accuracy,
             "clocks": clk, "gpu_launches": 2 * n * blk["blocks"],  # statistics + LCP kernel per step, every block
             "gpu": torch.cuda.get_device_name(dev),
         }
@@ -787,32 +813,19 @@ def ocean_arm(args):
     def step():
         lib.lcp_fused_ws(u, v, iso, 1.0, 1.0, 1, out=out)
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local).start()
-    time.sleep(0.35)
     n = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
-    if pg:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    t_wall0 = time.time()
-    for i in range(n):
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    t_wall1 = time.time()
-    if pg:
-        torch.distributed.barrier()
-    time.sleep(0.25)
-    clocks.stop()
-    total_ms = max_over_ranks(ev[0][0].elapsed_time(ev[-1][1]), device=dev)
-    kern_ms = sum(a.elapsed_time(b) for a, b in ev) / n
-    ms_per_step = total_ms / n
+    block_ms, blk, clk = timed_blocks(torch, step, n, args.warmup, local, pg, dev)
+    kern_ms = blk["block_ms_median"] / n
+    ms_per_step = block_ms / n
     value = weak_scaling_value(Hc * Wc, world, ms_per_step)
     alg = 2 * Mm * Hh * Ww * 2 + Kk * Hc * Wc * 4
+    accuracy = None
+    if rank == 0:  # the map of the last timed step on three crops (the oracle sees the same bf16-rounded members)
+        cw = min(Ww, 1024)
+        accuracy = crop_accuracy(out, lambda r0, r1, c0, c1: (u[:, r0:r1, c0:c1].float().cpu().numpy(),
+                                                               v[:, r0:r1, c0:c1].float().cpu().numpy()),
+                                 Hh, Ww, iso, [(0, min(Hh, 24), 0, cw), (Hh // 2 - 12, Hh // 2 + 12, Ww - cw, Ww),
+                                               (Hh - min(Hh, 24), Hh, Ww // 2 - cw // 2, Ww // 2 + cw // 2)])
     peak, peak_kind = measured_hbm_peak()
     achieved = alg / (kern_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -843,11 +856,12 @@ def ocean_arm(args):
             "dtype": "bf16 members, f32 arithmetic", "data": "synthetic",
             "config": {"workload": OCEAN_WORKLOAD if Hh == 8192 else f"{Hh} rows of: " + OCEAN_WORKLOAD, "H": Hh, "W": Ww, "M": Mm, "K": Kk, "global_batch": world,
                        "parallelism": f"independent fields x{world}" if world > 1 else "single",
-                       "l2": f"no flush: inputs {2 * Mm * Hh * Ww * 2 / 1e9:.1f} GB > 129 MB L2", "lcp_values_per_s": value * Kk,
+                       "l2": f"no flush: inputs {2 * Mm * Hh * Ww * 2 / 1e9:.1f} GB > 129 MB L2", "timing": blk,
+                       "lcp_values_per_s": value * Kk,
                        "hbm_frac_of_measured": roof["frac"]},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": None,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": None, "accuracy": accuracy,
             "e2e_note": "not measured for this line: 5.4 GB of members per step would be pinned on the host",
-            "clocks": clocks.summary(t_wall0, t_wall1), "gpu_launches": 2 * ws_row_bands(lib, Mm, Hh, Ww) * n,
+            "clocks": clk, "gpu_launches": 2 * ws_row_bands(lib, Mm, Hh, Ww) * n * blk["blocks"],
             "gpu": torch.cuda.get_device_name(dev),
         }
         print(json.dumps(line), flush=True)

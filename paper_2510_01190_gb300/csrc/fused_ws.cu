@@ -281,7 +281,51 @@ struct RowsParams {
     int64_t n_begin;      // statistics grid geometry, to recompute each band's requirement
     int sv;
     long long budget;     // clock cycles before a dependency wait gives up
+    double dsx2, dsx1, dsy2, dsy1;  // the stencil factors in FP64 (flagged vertices, below)
 };
+
+inline void set_spacing(RowsParams& rp, double dx, double dy) {
+    rp.sp = make_spacing(dx, dy);
+    rp.dsx2 = 0.5 / dx;
+    rp.dsx1 = 1.0 / dx;
+    rp.dsy2 = 0.5 / dy;
+    rp.dsy1 = 1.0 / dy;
+}
+
+// The divergence mean of a vertex as an unevaluated pair (mu, lo).  The fp32
+// stencil rounds the difference of the member-0 values x0 across it with an
+// error up to 2^-24 of that difference (exact when the two are within a factor
+// of 2), and mu itself keeps 24 bits: both are negligible unless the
+// difference is large against sigma, as when a mean of large magnitude
+// changes sign across the stencil.  Where A = |dx0_u| sx + |dx0_v| sy exceeds
+// 16 sigma (A^2 > 256 var, or any A > 0 at zero variance), the mean is formed
+// again in FP64 -- the fp32 x0 and delta differences are exact there -- and
+// split into mu + lo; elsewhere lo = 0 and mu is the fp32 value, unchanged.
+// With A <= 16 sigma the fp32 stencil moves a z-score by at most ~3 2^-24 16,
+// about 3e-6, and the LCP by about 1e-5 in the worst alignment.  Warp-uniform
+// (every lane of the warp must call it); the FP64 branch runs only in warps
+// with a flagged lane.
+// |dx0_u| sx + |dx0_v| sy above kExactZ / (sigma sqrt 2), i.e. above 16 sigma, takes the FP64 stencil.
+constexpr float kExactZ = 11.3137085f;  // 16 / sqrt(2)
+__device__ __forceinline__ bool mu_needs_fp64(float var, const float4& L, const float4& R, const float4& Vlo,
+                                              const float4& Vhi, float sx, float sy) {
+    const float A = fmaf(fabsf(R.x - L.x), sx, fabsf(Vhi.x - Vlo.x) * sy);
+    return A * A > 256.0f * var;
+}
+__device__ __forceinline__ float mu_fp64(float& mu, const float4& L, const float4& R, const float4& Vlo,
+                                         const float4& Vhi, double dsx, double dsy) {
+    const double m = (((double)R.x - (double)L.x) + ((double)R.y - (double)L.y)) * dsx +
+                     (((double)Vhi.x - (double)Vlo.x) + ((double)Vhi.y - (double)Vlo.y)) * dsy;
+    mu = (float)m;
+    return (float)(m - (double)mu);
+}
+__device__ __forceinline__ float exact_mu(float& mu, float var, const float4& L, const float4& R, const float4& Vlo,
+                                          const float4& Vhi, float sx, float sy, double dsx, double dsy) {
+    const bool big = mu_needs_fp64(var, L, R, Vlo, Vhi, sx, sy);
+    float lo = 0.0f;
+    if (__any_sync(0xFFFFFFFFu, big) && big) lo = mu_fp64(mu, L, R, Vlo, Vhi, dsx, dsy);
+    return lo;
+}
 
 // Bounded wait (thread 0 of the block) until the statistics rows of LCP row
 // band `by` are complete; every thread returns whether the wait gave up.
@@ -371,11 +415,13 @@ __global__ void __launch_bounds__(kRT, KX <= 4 ? 3 : (KX <= 16 ? 2 : 1))
     const bool ok = i < Wc;
     const bool one_sided_x = ic == 0 || ic == W - 1;
     const float sx = one_sided_x ? p.sp.sx1 : p.sp.sx2, sxq = one_sided_x ? p.sp.sx1q : p.sp.sx2q;
+    const double dsx = one_sided_x ? p.dsx1 : p.dsx2;
     const bool edge_lane = lane == 0 || lane == 31;
     const int iedge = lane == 0 ? max(ic - 1, 0) : min(ic + 1, W - 1);  // warp-edge neighbour column
     const int ix = min(c0 + kRT, W - 1);                                  // the tile's extra right vertex
     const bool one_sided_xx = ix == 0 || ix == W - 1;
     const float sx_x = one_sided_xx ? p.sp.sx1 : p.sp.sx2, sxq_x = one_sided_xx ? p.sp.sx1q : p.sp.sx2q;
+    const double dsx_x = one_sided_xx ? p.dsx1 : p.dsx2;
     const int wi = (c0 >> 5) + warp;
     const bool word_writer = MASK && lane == 0 && wi < p.n_words;
     float c[KX];
@@ -421,23 +467,28 @@ __global__ void __launch_bounds__(kRT, KX <= 4 ? 3 : (KX <= 16 ? 2 : 1))
         const float sy = one_sided_y ? p.sp.sy1 : p.sp.sy2, syq = one_sided_y ? p.sp.sy1q : p.sp.sy2q;
         const float4 Vlo = j > 0 ? VM : V0;
         const float4 Vhi = j < H - 1 ? VP : V0;
-        const float mu = fmaf((R.x - L.x) + (R.y - L.y), sx, ((Vhi.x - Vlo.x) + (Vhi.y - Vlo.y)) * sy);
+        float mu = fmaf((R.x - L.x) + (R.y - L.y), sx, ((Vhi.x - Vlo.x) + (Vhi.y - Vlo.y)) * sy);
         const float var = fmaf(R.z + L.z, sxq, (Vhi.z + Vlo.z) * syq);
+        const double dsy = one_sided_y ? p.dsy1 : p.dsy2;
+        const float lo = exact_mu(mu, var, L, R, Vlo, Vhi, sx, sy, dsx, dsy);
         // phase A: its (p, q) and class bit for every isovalue
         {
             const bool zero = var == 0.0f;
             const float s = rsqrtf(2.0f * var);
             uint32_t b = 0;
             if constexpr (KX == 1) {
-                const bool below = mu < c[0];
-                pq[t] = vertex_pq(mu, s, zero, c[0], below);
+                const float d = (mu - c[0]) + lo;  // mu - c with the low part of the mean
+                const bool below = d < 0.0f;
+                pq[t] = vertex_pq_d(d, s, zero, below);
                 b = below;
             } else {
 #pragma unroll
                 for (int k = 0; k < KX; k += 2) {
-                    const bool below0 = mu < c[k], below1 = mu < c[k + 1];
+                    const float2 d = __fadd2_rn(__fadd2_rn(make_float2(mu, mu), make_float2(-c[k], -c[k + 1])),
+                                                make_float2(lo, lo));
+                    const bool below0 = d.x < 0.0f, below1 = d.y < 0.0f;
                     float2 a0, a1;
-                    vertex_pq2(mu, s, zero, make_float2(c[k], c[k + 1]), below0, below1, a0, a1);
+                    vertex_pq2_d(d, s, zero, below0, below1, a0, a1);
                     pq[k * NV + t] = a0;
                     pq[(k + 1) * NV + t] = a1;
                     b |= ((uint32_t)below0 << k) | ((uint32_t)below1 << (k + 1));
@@ -447,14 +498,16 @@ __global__ void __launch_bounds__(kRT, KX <= 4 ? 3 : (KX <= 16 ? 2 : 1))
         }
         if (last_warp) {  // the extra right vertex: gathered from lanes 0-3, isovalues spread over the lanes
             const float4 up = shfl_rec(Xc, 0), ul = shfl_rec(Xc, 1), vh = shfl_rec(Xc, 2), vl = shfl_rec(Xc, 3);
-            const float mux = fmaf((up.x - ul.x) + (up.y - ul.y), sx_x, ((vh.x - vl.x) + (vh.y - vl.y)) * sy);
+            float mux = fmaf((up.x - ul.x) + (up.y - ul.y), sx_x, ((vh.x - vl.x) + (vh.y - vl.y)) * sy);
             const float varx = fmaf(up.z + ul.z, sxq_x, (vh.z + vl.z) * syq);
+            const float lox = exact_mu(mux, varx, ul, up, vl, vh, sx_x, sy, dsx_x, dsy);
             float cl = 0.0f;
 #pragma unroll
             for (int k = 0; k < KX; ++k)
                 if (k == lane) cl = c[k];
-            const bool below = mux < cl;
-            if (lane < KX) pq[lane * NV + kRT] = vertex_pq(mux, rsqrtf(2.0f * varx), varx == 0.0f, cl, below);
+            const float dxk = (mux - cl) + lox;
+            const bool below = dxk < 0.0f;
+            if (lane < KX) pq[lane * NV + kRT] = vertex_pq_d(dxk, rsqrtf(2.0f * varx), varx == 0.0f, below);
             const uint32_t bx = __ballot_sync(0xFFFFFFFFu, lane < KX && below);
             if (lane == 0) cls[kRT] = bx;
         }
@@ -533,11 +586,13 @@ __global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer
     const bool ok = i < Wc;
     const bool osx = ic == 0 || ic == W - 1;
     const float sx = osx ? p.sp.sx1 : p.sp.sx2, sxq = osx ? p.sp.sx1q : p.sp.sx2q;
+    const double dsx = osx ? p.dsx1 : p.dsx2;
     const bool edge_lane = lane == 0 || lane == 31;
     const int iedge = lane == 0 ? max(ic - 1, 0) : min(ic + 1, W - 1);
     const int ix = min(c0w + 32, W - 1);  // the warp's 33rd vertex
     const bool osxx = ix == 0 || ix == W - 1;
     const float sx_x = osxx ? p.sp.sx1 : p.sp.sx2, sxq_x = osxx ? p.sp.sx1q : p.sp.sx2q;
+    const double dsx_x = osxx ? p.dsx1 : p.dsx2;
     const int ixl = max(ix - 1, 0), ixr = min(ix + 1, W - 1);
     const int wi = c0w >> 5;
     float c[KX];
@@ -578,8 +633,8 @@ __global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer
     OutT* const obase = reinterpret_cast<OutT*>(p.out);
     Off oo = (Off)p.kbase * plane + (Off)(a - 1) * (Off)Wc + (Off)i;  // row a - 1: advanced before the first store
     Off mo = MASK ? ((Off)p.kbase * (Off)Hc + (Off)(a - 1)) * (Off)p.n_words + (Off)wi : (Off)0;
-#pragma unroll
-    for (int jj = 0; jj <= kTR; ++jj) {  // vertex rows a .. e (at most kTR + 1), unrolled: no window moves
+#pragma unroll 1
+    for (int jj = 0; jj <= kTR; ++jj) {  // vertex rows a .. e (at most kTR + 1); a rolled loop keeps the code small
         const int j = a + jj;
         if (j > e) break;
         const RowRec C = R0;
@@ -598,31 +653,44 @@ __global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer
         if (ic == W - 1) R = C.U;
         const float4 Vlo = j > 0 ? VM : V0;
         const float4 Vhi = j < H - 1 ? VP : V0;
-        const float mu = fmaf((R.x - L.x) + (R.y - L.y), sx, ((Vhi.x - Vlo.x) + (Vhi.y - Vlo.y)) * sy);
+        float mu = fmaf((R.x - L.x) + (R.y - L.y), sx, ((Vhi.x - Vlo.x) + (Vhi.y - Vlo.y)) * sy);
         const float var = fmaf(R.z + L.z, sxq, (Vhi.z + Vlo.z) * syq);
         // the 33rd vertex (every lane, from lanes 0..3's records); (ixl, ixr) and the clamped rows
         // already are the one-sided stencil at the edges
         const float4 XLc = shfl_rec(C.X, 0), XRc = shfl_rec(C.X, 1), XDc = shfl_rec(C.X, 2), XUc = shfl_rec(C.X, 3);
-        const float mux = fmaf((XRc.x - XLc.x) + (XRc.y - XLc.y), sx_x, ((XUc.x - XDc.x) + (XUc.y - XDc.y)) * sy);
+        float mux = fmaf((XRc.x - XLc.x) + (XRc.y - XLc.y), sx_x, ((XUc.x - XDc.x) + (XUc.y - XDc.y)) * sy);
         const float varx = fmaf(XRc.z + XLc.z, sxq_x, (XUc.z + XDc.z) * syq);
         const bool zero = var == 0.0f;
-        const float s = rsqrtf(2.0f * var);
+        const float s = rsqrtf(2.0f * var), sxv = rsqrtf(2.0f * varx);
+        // member-0 differences across the stencil of more than 16 sigma: the mean again in FP64, as mu + lo
+        float lo = 0.0f, lox = 0.0f;
+        const bool big = !(fmaf(fabsf(R.x - L.x), sx, fabsf(Vhi.x - Vlo.x) * sy) * s <= kExactZ);
+        const bool bigx = !(fmaf(fabsf(XRc.x - XLc.x), sx_x, fabsf(XUc.x - XDc.x) * sy) * sxv <= kExactZ);
+        if (__any_sync(0xFFFFFFFFu, big || bigx)) {
+            const double dsy = osy ? p.dsy1 : p.dsy2;
+            if (big) lo = mu_fp64(mu, L, R, Vlo, Vhi, dsx, dsy);
+            if (bigx) lox = mu_fp64(mux, XLc, XRc, XDc, XUc, dsx_x, dsy);
+        }
         float2 pq[KX];
         uint32_t b = 0;
         if constexpr (KX == 1) {
-            const bool below = mu < c[0];
-            pq[0] = vertex_pq(mu, s, zero, c[0], below);
+            const float d = (mu - c[0]) + lo;  // mu - c with the low part of the mean
+            const bool below = d < 0.0f;
+            pq[0] = vertex_pq_d(d, s, zero, below);
             b = below;
         } else {
 #pragma unroll
             for (int k = 0; k < KX; k += 2) {
-                const bool b0 = mu < c[k], b1 = mu < c[k + 1];
-                vertex_pq2(mu, s, zero, make_float2(c[k], c[k + 1]), b0, b1, pq[k], pq[k + 1]);
+                const float2 d = __fadd2_rn(__fadd2_rn(make_float2(mu, mu), make_float2(-c[k], -c[k + 1])),
+                                            make_float2(lo, lo));
+                const bool b0 = d.x < 0.0f, b1 = d.y < 0.0f;
+                vertex_pq2_d(d, s, zero, b0, b1, pq[k], pq[k + 1]);
                 b |= ((uint32_t)b0 << k) | ((uint32_t)b1 << (k + 1));
             }
         }
-        const bool belowx = mux < cl;
-        const float2 pqx = vertex_pq(mux, rsqrtf(2.0f * varx), varx == 0.0f, cl, belowx);
+        const float dx_ = (mux - cl) + lox;
+        const bool belowx = dx_ < 0.0f;
+        const float2 pqx = vertex_pq_d(dx_, sxv, varx == 0.0f, belowx);
         const uint32_t bx = __ballot_sync(0xFFFFFFFFu, lane < KX && belowx);
         uint32_t bn = __shfl_down_sync(0xFFFFFFFFu, b, 1);
         if (lane == 31) bn = bx;
@@ -855,7 +923,7 @@ lcp_status run(const void* u, const void* v, int M, int H, int W, int64_t stride
         rp.W = W;
         rp.r_begin = r0;
         rp.r_end = r1;
-        rp.sp = make_spacing(dx, dy);
+        set_spacing(rp, dx, dy);
         rp.out = out;
         rp.mask = mask;
         rp.n_words = (W - 1 + 31) / 32;
@@ -892,7 +960,7 @@ lcp_status ws_lcp_rows(const float4* rec, int64_t ps, int row0, int H, int W, in
     rp.W = W;
     rp.r_begin = r0;
     rp.r_end = r1;
-    rp.sp = make_spacing(dx, dy);
+    set_spacing(rp, dx, dy);
     rp.out = out;
     rp.mask = mask;
     rp.n_words = (W - 1 + 31) / 32;
@@ -989,7 +1057,7 @@ extern "C" lcp_status lcp_test_stalled_lcp_wait(int H, int W, const float* iso, 
     rp.W = W;
     rp.r_begin = 0;
     rp.r_end = r1;
-    rp.sp = make_spacing(1.0, 1.0);
+    set_spacing(rp, 1.0, 1.0);
     rp.out = lcp_out;
     rp.mask = mask;
     rp.n_words = (W - 1 + 31) / 32;

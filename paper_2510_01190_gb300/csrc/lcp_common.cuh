@@ -212,6 +212,28 @@ __device__ __forceinline__ void vertex_pq2(float mu, float s, bool zero, float2 
     pq1 = make_float2(pos1 ? e.y : 1.0f - e.y, pos1 ? 1.0f - e.y : e.y);
 }
 
+// The same pair from d = mu - c given directly (t = d s): for a mean carried as
+// hi + lo, d = (hi - c) + lo keeps the digits that hi alone cannot hold.
+__device__ __forceinline__ float2 vertex_pq_d(float d, float s, bool zero, bool below) {
+    float t = d * s;
+    if (zero) t = below ? -1.0e4f : 1.0e4f;
+    const float e = half_erfc_nonneg(fabsf(t));
+    const bool pos = t >= 0.0f;
+    return make_float2(pos ? e : 1.0f - e, pos ? 1.0f - e : e);
+}
+__device__ __forceinline__ void vertex_pq2_d(float2 d, float s, bool zero, bool below0, bool below1, float2& pq0,
+                                             float2& pq1) {
+    float2 t = __fmul2_rn(d, make_float2(s, s));
+    if (zero) {
+        t.x = below0 ? -1.0e4f : 1.0e4f;
+        t.y = below1 ? -1.0e4f : 1.0e4f;
+    }
+    const float2 e = half_erfc_nonneg2(make_float2(fabsf(t.x), fabsf(t.y)));
+    const bool pos0 = t.x >= 0.0f, pos1 = t.y >= 0.0f;
+    pq0 = make_float2(pos0 ? e.x : 1.0f - e.x, pos0 ? 1.0f - e.x : e.x);
+    pq1 = make_float2(pos1 ? e.y : 1.0f - e.y, pos1 ? 1.0f - e.y : e.y);
+}
+
 // Clamp to [0, 1] with NaN propagated (max.NaN / min.NaN).
 __device__ __forceinline__ float clamp01_nan(float x) {
     float r;

@@ -474,3 +474,42 @@ def test_row_strips_reassemble_the_whole_map(lib, n):
     assert [p[0] for p in parts] == [lib.lcp_strip_plan(203, n, r)[2] for r in range(n)]
     assert torch.equal(torch.cat([p[1] for p in parts], dim=1), whole)
     assert torch.equal(torch.cat([p[2] for p in parts], dim=1), wmask)
+
+
+def _sign_changing_field(h, w, m, seed, amp=1e4, sigma=0.05):
+    """Means of magnitude amp whose sign flips across every central stencil
+    (columns +, +, -, - repeating for u, rows for v; |mean| / sigma = 2e5) with
+    a gentle smooth part, and Gaussian member noise sigma."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    sx = np.array([1.0, 1.0, -1.0, -1.0])[np.arange(w) % 4]
+    sy = np.array([1.0, -1.0, -1.0, 1.0])[np.arange(h) % 4]
+    y, x = np.mgrid[0:h, 0:w].astype(np.float64)
+    mu_u = amp * sx[None, :] + 0.3 * np.sin(x / 5.0 + y / 7.0)
+    mu_v = amp * sy[:, None] + 0.3 * np.cos(x / 6.0 - y / 4.0)
+    u = (mu_u[None] + sigma * g.standard_normal((m, h, w))).astype(np.float32)
+    v = (mu_v[None] + sigma * g.standard_normal((m, h, w))).astype(np.float32)
+    return u, v
+
+
+@pytest.mark.parametrize("dx,dy", [(1.0, 1.0), (0.7, 1.3)])
+@pytest.mark.parametrize("k", [1, 5, 12])
+def test_fused_ws_sign_changing_large_means(lib, dx, dy, k):
+    """Means of 1e4 whose sign changes across the stencil (sigma = 0.05) and
+    isovalues placed within a few sigma of chosen vertices' mu_d: the fp32
+    difference of member-0 values would move z-scores by ~1e-2 here; the
+    flagged FP64 stencil keeps the map within 1e-5 of the FP64 oracle and the
+    mask exact outside the rounding guard band."""
+    h, w, m = 45, 70, 12
+    u, v = _sign_changing_field(h, w, m, seed=17)
+    ref0 = O.lcp_closed_form(u, v, dx, dy, [0.0])
+    g = np.random.Generator(np.random.PCG64(k))
+    picks = g.integers(0, h * w, size=k)
+    sd = np.sqrt(ref0["var_d"].reshape(-1)[picks])
+    iso = (ref0["mu_d"].reshape(-1)[picks] + g.uniform(-2.0, 2.0, size=k) * sd).astype(np.float32)
+    lcp, mask = lib.lcp_fused_ws(_dev(u), _dev(v), iso, dx, dy, mask=True)
+    ref = O.lcp_closed_form(u, v, dx, dy, iso)
+    err = np.abs(_np(lcp) - ref["lcp"])
+    assert np.max(err) <= LCP_TOL, float(np.max(err))
+    assert np.count_nonzero((ref["lcp"] > 1e-3) & (ref["lcp"] < 1 - 1e-3)) > 10  # the isovalues are really near mu_d
+    guard = _oracle_mask_guard(ref["mu_d"], iso)
+    assert np.array_equal(lib.unpack_mask(mask, w).cpu().numpy()[guard], ref["mask"][guard])
