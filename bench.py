@@ -60,7 +60,7 @@ def parse():
                          "empirical LCP of the non-Gaussian field")
     ap.add_argument("--tile", type=str, default=None,
                     help="batch workload: force the tile shape ROWS,COLS instead of autotuning")
-    ap.add_argument("--train-epochs", type=int, default=20, help="learned workload: training epochs (untimed)")
+    ap.add_argument("--train-epochs", type=int, default=40, help="learned workload: training epochs (untimed)")
     ap.add_argument("--split", choices=["fields", "rows"], default="fields",
                     help="latlon under torchrun: each rank its own field (weak scaling) or one field in row "
                          "strips with halo re-reads, no exchange (strong scaling)")
@@ -594,10 +594,10 @@ def learned_arm(args):
     from paper_2510_01190_gb300 import synth
 
     lib.load()
-    # training (not timed): two other non-Gaussian fields, empirical-mode MC labels at S = 1e4
+    # training (not timed): five other non-Gaussian fields, empirical-mode MC labels at S = 1e4
     t_train0 = time.perf_counter()
     parts = []
-    for seed, hh, ww in ((1, 384, 384), (3, 192, 256)):
+    for seed, hh, ww in ((1, 384, 384), (3, 192, 256), (4, 384, 384), (5, 384, 384), (7, 384, 384)):
         dd = synth.non_gaussian_ensemble(seed, h=hh, w=ww, m=50, k=8)
         uu, vv = torch.from_numpy(dd["u"]).to(dev), torch.from_numpy(dd["v"]).to(dev)
         ft, pr = G.lcp_surrogate_features(G.lcp_moments(uu, vv), dd["isovalues"])

@@ -364,6 +364,23 @@ lcp_status lcp_mlp_backward(const float* params, const void* feat, const float* 
                             int64_t n, float* grad, float* loss, lcp_stream_t stream);
 
 /*
+ * lcp_mlp_backward_ws - lcp_mlp_backward with a result that is the same, bit
+ * for bit, on every run on a device: each CTA sums its rows in a fixed order
+ * (its warps' partial vectors added in warp order) and writes its partial
+ * gradient to its own row of the workspace, and a second kernel adds the rows
+ * in CTA order.  Training with it (and the element-wise Adam step) is
+ * reproducible, so a run resumed from a checkpoint continues exactly as the
+ * uninterrupted run.  workspace: device, 16-byte aligned, at least
+ * lcp_mlp_backward_workspace_bytes(n) bytes (about 25 KB per CTA, at most
+ * two CTAs per SM); grad and loss are overwritten.  The paper has no
+ * counterpart (the surrogate is this library's addition).
+ */
+size_t lcp_mlp_backward_workspace_bytes(int64_t n);
+lcp_status lcp_mlp_backward_ws(const float* params, const void* feat, const float* prior, const float* target,
+                               int64_t n, float* grad, float* loss, void* workspace, size_t workspace_bytes,
+                               lcp_stream_t stream);
+
+/*
  * lcp_adam_step - one Adam update (Kingma and Ba, ICLR 2015, Algorithm 1) of n
  * fp32 parameters in place: m, v (device, n floats each, zero before step 1)
  * are the moving averages of grad and grad^2, bias-corrected with step count

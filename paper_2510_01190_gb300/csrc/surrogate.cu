@@ -714,9 +714,11 @@ struct BwdSmem {
     __align__(16) __nv_bfloat16 h1s[64 * kW2S];
     __align__(16) __nv_bfloat16 d1s[64 * kW2S];
     __align__(16) __nv_bfloat16 d2s[64 * kW2S];
-    __align__(16) float db1[kHid];
-    float db2[kHid], dw3[kHid];
-    float db3, loss;
+    // per-warp partial sums (each written by one warp only, summed in warp order at the end), so the
+    // block's result does not depend on the order in which its warps run
+    __align__(16) float db1[kMT / 32][kHid];
+    float db2[kMT / 32][kHid], dw3[kMT / 32][kHid];
+    float db3[kMT / 32], loss[kMT / 32];
 };
 
 static_assert(offsetof(BwdSmem, xs) % 16 == 0 && offsetof(BwdSmem, h1s) % 16 == 0 &&
@@ -736,16 +738,28 @@ __device__ __forceinline__ float sum_over_gid(float x) {
     return x;
 }
 
+// One CTA's gradient sums go either straight into grad (atomic adds, scaled by
+// 1/n) or, for the deterministic variant, unscaled into its own row `part` of
+// [gridDim.x][kPartStride] floats (every entry written), which
+// bwd_reduce_kernel then sums over the CTAs in CTA order.
+constexpr int kPartStride = LCP_MLP_NPARAMS + 4;  // the parameters, then the loss (16-byte rows)
+
+template <bool DET>
 __global__ void __launch_bounds__(kMT) mlp_backward_kernel(const float* __restrict__ prm,
                                                           const __nv_bfloat16* __restrict__ feat,
                                                           const float* __restrict__ prior,
                                                           const float* __restrict__ target, int64_t n,
-                                                          float* __restrict__ grad, float* __restrict__ loss) {
+                                                          float* __restrict__ grad, float* __restrict__ loss,
+                                                          float* __restrict__ parts) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
     load_net(prm, S.net, S.W2t);
-    for (int q = threadIdx.x; q < kHid; q += blockDim.x) S.db1[q] = S.db2[q] = S.dw3[q] = 0.f;
-    if (threadIdx.x == 0) S.db3 = S.loss = 0.f;
+    for (int q = threadIdx.x; q < (kMT / 32) * kHid; q += blockDim.x) {
+        (&S.db1[0][0])[q] = 0.f;
+        (&S.db2[0][0])[q] = 0.f;
+        (&S.dw3[0][0])[q] = 0.f;
+    }
+    if (threadIdx.x < kMT / 32) S.db3[threadIdx.x] = S.loss[threadIdx.x] = 0.f;
     __syncthreads();
     const NetSmem& s = S.net;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
@@ -785,10 +799,15 @@ __global__ void __launch_bounds__(kMT) mlp_backward_kernel(const float* __restri
         // d(sum of squared errors)/dz3 = 2 (y - t) y (1 - y); the 1/n of the mean is applied once at the end
         const float dlo = vlo ? 2.f * (ylo - tlo) * ylo * (1.f - ylo) : 0.f;
         const float dhi = vhi ? 2.f * (yhi - thi) * yhi * (1.f - yhi) : 0.f;
-        if (tig == 0) {
-            const float e = (vlo ? (ylo - tlo) * (ylo - tlo) : 0.f) + (vhi ? (yhi - thi) * (yhi - thi) : 0.f);
-            atomicAdd(&S.loss, e);
-            atomicAdd(&S.db3, dlo + dhi);
+        {  // the warp's sums over its 16 rows (each row once: the lanes with tig == 0), fixed order
+            const float e = tig == 0 ? (vlo ? (ylo - tlo) * (ylo - tlo) : 0.f) + (vhi ? (yhi - thi) * (yhi - thi) : 0.f)
+                                     : 0.f;
+            const float dd = tig == 0 ? dlo + dhi : 0.f;
+            const float es = sum_over_gid(e), ds = sum_over_gid(dd);
+            if (lane == 0) {
+                S.loss[warp] += es;
+                S.db3[warp] += ds;
+            }
         }
         // stage h1 (its A fragments are C fragments of 8-column tiles 2ks, 2ks+1)
 #pragma unroll
@@ -811,9 +830,9 @@ __global__ void __launch_bounds__(kMT) mlp_backward_kernel(const float* __restri
                 dz[2 + e] = dhi * w * (1.f - h2[nt][2 + e] * h2[nt][2 + e]);
                 const float gw3 = sum_over_gid(h2[nt][e] * dlo + h2[nt][2 + e] * dhi);
                 const float gb2 = sum_over_gid(dz[e] + dz[2 + e]);
-                if (gid == 0) {
-                    atomicAdd(&S.dw3[col], gw3);
-                    atomicAdd(&S.db2[col], gb2);
+                if (gid == 0) {  // one lane per column of this warp
+                    S.dw3[warp][col] += gw3;
+                    S.db2[warp][col] += gb2;
                 }
             }
             const uint32_t lo = pack_bf16(dz[0], dz[1]), hi = pack_bf16(dz[2], dz[3]);
@@ -845,8 +864,8 @@ __global__ void __launch_bounds__(kMT) mlp_backward_kernel(const float* __restri
             st_pair(S.d1s, rw + gid + 8, 8 * nt + 2 * tig, kW2S, pack_bf16(z2, z3));
             const float g0 = sum_over_gid(z0 + z2), g1 = sum_over_gid(z1 + z3);
             if (gid == 0) {
-                atomicAdd(&S.db1[8 * nt + 2 * tig], g0);
-                atomicAdd(&S.db1[8 * nt + 2 * tig + 1], g1);
+                S.db1[warp][8 * nt + 2 * tig] += g0;
+                S.db1[warp][8 * nt + 2 * tig + 1] += g1;
             }
         }
         __syncthreads();
@@ -876,15 +895,21 @@ __global__ void __launch_bounds__(kMT) mlp_backward_kernel(const float* __restri
         }
         __syncthreads();
     }
-    // add this CTA's sums to the output
+    // this CTA's sums: the weight matrices from this warp's registers (its own 16 output rows), the
+    // vectors from the per-warp partials in warp order
+    float* const row = DET ? parts + (int64_t)blockIdx.x * kPartStride : nullptr;
+    auto put = [&](int idx, float val) {
+        if (DET) row[idx] = val;
+        else atomicAdd(grad + idx, val * inv_n);
+    };
     const int o0 = 16 * warp;
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int col = 8 * nt + 2 * tig + e;
-            atomicAdd(grad + kOffW2 + (o0 + gid) * kHid + col, gW2[nt][e] * inv_n);
-            atomicAdd(grad + kOffW2 + (o0 + gid + 8) * kHid + col, gW2[nt][2 + e] * inv_n);
+            put(kOffW2 + (o0 + gid) * kHid + col, gW2[nt][e]);
+            put(kOffW2 + (o0 + gid + 8) * kHid + col, gW2[nt][2 + e]);
         }
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt)
@@ -892,19 +917,51 @@ __global__ void __launch_bounds__(kMT) mlp_backward_kernel(const float* __restri
         for (int e = 0; e < 2; ++e) {
             const int col = 8 * nt + 2 * tig + e;
             if (col < 17) {
-                atomicAdd(grad + kOffW1 + (o0 + gid) * kFS + col, gW1[nt][e] * inv_n);
-                atomicAdd(grad + kOffW1 + (o0 + gid + 8) * kFS + col, gW1[nt][2 + e] * inv_n);
+                put(kOffW1 + (o0 + gid) * kFS + col, gW1[nt][e]);
+                put(kOffW1 + (o0 + gid + 8) * kFS + col, gW1[nt][2 + e]);
+            } else if (DET) {  // the zero columns of W1: every entry of the row is written
+                row[kOffW1 + (o0 + gid) * kFS + col] = 0.f;
+                row[kOffW1 + (o0 + gid + 8) * kFS + col] = 0.f;
             }
         }
     __syncthreads();
     for (int q = threadIdx.x; q < kHid; q += blockDim.x) {
-        atomicAdd(grad + kOffB1 + q, S.db1[q] * inv_n);
-        atomicAdd(grad + kOffB2 + q, S.db2[q] * inv_n);
-        atomicAdd(grad + kOffW3 + q, S.dw3[q] * inv_n);
+        float a = 0.f, b = 0.f, c = 0.f;
+#pragma unroll
+        for (int w = 0; w < kMT / 32; ++w) {
+            a += S.db1[w][q];
+            b += S.db2[w][q];
+            c += S.dw3[w][q];
+        }
+        put(kOffB1 + q, a);
+        put(kOffB2 + q, b);
+        put(kOffW3 + q, c);
     }
     if (threadIdx.x == 0) {
-        atomicAdd(grad + kOffB3, S.db3 * inv_n);
-        if (loss) atomicAdd(loss, S.loss * inv_n);
+        float a = 0.f, l = 0.f;
+#pragma unroll
+        for (int w = 0; w < kMT / 32; ++w) {
+            a += S.db3[w];
+            l += S.loss[w];
+        }
+        put(kOffB3, a);
+        if (DET) {
+            for (int q = kOffB3 + 1; q < LCP_MLP_NPARAMS; ++q) row[q] = 0.f;  // padding
+            row[LCP_MLP_NPARAMS] = l;
+        } else if (loss) {
+            atomicAdd(loss, l * inv_n);
+        }
+    }
+}
+
+// grad[q] = (sum over CTAs, in CTA order, of their partial q) / n; the loss likewise.
+__global__ void bwd_reduce_kernel(const float* __restrict__ parts, int nparts, float inv_n, float* __restrict__ grad,
+                                  float* __restrict__ loss) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q <= LCP_MLP_NPARAMS; q += gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int b = 0; b < nparts; ++b) acc += parts[(int64_t)b * kPartStride + q];
+        if (q < LCP_MLP_NPARAMS) grad[q] = acc * inv_n;
+        else if (loss) *loss = acc * inv_n;
     }
 }
 
@@ -1000,37 +1057,77 @@ extern "C" lcp_status lcp_mlp_forward(const float* params, const void* feat, con
     return check_launch("lcp_mlp_forward");
 }
 
-extern "C" lcp_status lcp_mlp_backward(const float* params, const void* feat, const float* prior, const float* target,
-                                       int64_t n, float* grad, float* loss, lcp_stream_t stream) {
-    if (!params || !feat || !target || !grad || n < 1 || !aligned16(feat))
-        return fail(LCP_ERR_ARG, "lcp_mlp_backward: NULL/misaligned pointer or n < 1");
-    cudaStream_t st = (cudaStream_t)stream;
+namespace {
+// Shared-memory size of both backward variants, set once per device.
+lcp_status prepare_backward(const char* fn) {
     static std::mutex mu;
     static bool set[64] = {false};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         cudaGetLastError();
-        return fail(LCP_ERR_CUDA, "lcp_mlp_backward: no usable current device");
+        return fail(LCP_ERR_CUDA, "%s: no usable current device", fn);
     }
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        if (!set[dev]) {
-            if (cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sizeof(BwdSmem)) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(LCP_ERR_CUDA, "lcp_mlp_backward: %zu bytes of shared memory not available", sizeof(BwdSmem));
-            }
-            set[dev] = true;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!set[dev]) {
+        if (cudaFuncSetAttribute(mlp_backward_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(BwdSmem)) != cudaSuccess ||
+            cudaFuncSetAttribute(mlp_backward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(BwdSmem)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LCP_ERR_CUDA, "%s: %zu bytes of shared memory not available", fn, sizeof(BwdSmem));
         }
+        set[dev] = true;
     }
+    return LCP_OK;
+}
+
+lcp_status check_backward(const char* fn, const float* params, const void* feat, const float* target, float* grad,
+                          int64_t n) {
+    if (!params || !feat || !target || !grad || n < 1 || !aligned16(feat))
+        return fail(LCP_ERR_ARG, "%s: NULL/misaligned pointer or n < 1", fn);
+    return LCP_OK;
+}
+}  // namespace
+
+extern "C" lcp_status lcp_mlp_backward(const float* params, const void* feat, const float* prior, const float* target,
+                                       int64_t n, float* grad, float* loss, lcp_stream_t stream) {
+    static const char* fn = "lcp_mlp_backward";
+    lcp_status s = check_backward(fn, params, feat, target, grad, n);
+    if (s != LCP_OK || (s = prepare_backward(fn)) != LCP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(grad, 0, LCP_MLP_NPARAMS * sizeof(float), st) != cudaSuccess ||
         (loss && cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess)) {
         cudaGetLastError();
-        return fail(LCP_ERR_CUDA, "lcp_mlp_backward: clearing the outputs failed");
+        return fail(LCP_ERR_CUDA, "%s: clearing the outputs failed", fn);
     }
-    mlp_backward_kernel<<<grid_for(n, 64, 2), kMT, sizeof(BwdSmem), st>>>(
-        params, (const __nv_bfloat16*)feat, prior, target, n, grad, loss);
-    return check_launch("lcp_mlp_backward");
+    mlp_backward_kernel<false><<<grid_for(n, 64, 2), kMT, sizeof(BwdSmem), st>>>(
+        params, (const __nv_bfloat16*)feat, prior, target, n, grad, loss, nullptr);
+    return check_launch(fn);
+}
+
+extern "C" size_t lcp_mlp_backward_workspace_bytes(int64_t n) {
+    if (n < 1) return 0;
+    return (size_t)grid_for(n, 64, 2) * kPartStride * sizeof(float);
+}
+
+extern "C" lcp_status lcp_mlp_backward_ws(const float* params, const void* feat, const float* prior,
+                                          const float* target, int64_t n, float* grad, float* loss, void* workspace,
+                                          size_t workspace_bytes, lcp_stream_t stream) {
+    static const char* fn = "lcp_mlp_backward_ws";
+    lcp_status s = check_backward(fn, params, feat, target, grad, n);
+    if (s != LCP_OK) return s;
+    const int grid = grid_for(n, 64, 2);
+    const size_t need = (size_t)grid * kPartStride * sizeof(float);
+    if (!workspace || !aligned16(workspace) || workspace_bytes < need)
+        return fail(LCP_ERR_ARG, "%s: need a 16-byte aligned workspace of %zu bytes", fn, need);
+    if ((s = prepare_backward(fn)) != LCP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float* parts = reinterpret_cast<float*>(workspace);
+    mlp_backward_kernel<true><<<grid, kMT, sizeof(BwdSmem), st>>>(params, (const __nv_bfloat16*)feat, prior, target,
+                                                                    n, grad, loss, parts);
+    if ((s = check_launch(fn)) != LCP_OK) return s;
+    bwd_reduce_kernel<<<(LCP_MLP_NPARAMS + 1 + 255) / 256, 256, 0, st>>>(parts, grid, 1.0f / (float)n, grad, loss);
+    return check_launch(fn);
 }
 
 extern "C" lcp_status lcp_adam_step(float* params, const float* grad, float* m, float* v, int64_t n, int t, float lr,

@@ -30,6 +30,7 @@ __all__ = [
     "lcp_surrogate_features",
     "lcp_mlp_forward",
     "lcp_mlp_backward",
+    "lcp_mlp_backward_ws",
     "lcp_adam_step",
     "lcp_mlp_infer",
     "Surrogate",
@@ -46,6 +47,8 @@ _SIGS = {
     "lcp_surrogate_features": (c_int, [c_vp, c_int, c_int, c_double, c_double, c_fp, c_int, c_vp, c_vp, c_vp]),
     "lcp_mlp_forward": (c_int, [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp]),
     "lcp_mlp_backward": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
+    "lcp_mlp_backward_workspace_bytes": (ctypes.c_size_t, [c_i64]),
+    "lcp_mlp_backward_ws": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, ctypes.c_size_t, c_vp]),
     "lcp_adam_step": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_int, c_float, c_float, c_float, c_float, c_vp]),
     "lcp_mlp_infer": (c_int, [c_vp, c_int, c_int, c_double, c_double, c_fp, c_int, c_vp, c_vp, c_int, c_vp]),
 }
@@ -130,6 +133,25 @@ def lcp_mlp_backward(params, feat, prior, target, grad=None, loss=None):
     return grad, loss
 
 
+def lcp_mlp_backward_ws(params, feat, prior, target, grad=None, loss=None, workspace=None):
+    """lcp_mlp_backward with a result that is bitwise the same on every run
+    (per-CTA partial sums reduced in CTA order through ``workspace``, a uint8
+    device tensor of lcp_mlp_backward_workspace_bytes(n); one is allocated if
+    none is given)."""
+    n = feat.shape[0]
+    lib = _lib()
+    if grad is None:
+        grad = torch.empty(MLP_NPARAMS, dtype=torch.float32, device=feat.device)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+    need = int(lib.lcp_mlp_backward_workspace_bytes(n))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=feat.device)
+    _check(lib.lcp_mlp_backward_ws(_ptr(params), _ptr(feat), _ptr(prior), _ptr(target), n, _ptr(grad), _ptr(loss),
+                                   _ptr(workspace), workspace.numel(), _stream()))
+    return grad, loss
+
+
 def lcp_adam_step(params, grad, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
                   eps: float = 1e-8):
     _check(_lib().lcp_adam_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), int(t), float(lr),
@@ -149,7 +171,10 @@ def lcp_mlp_infer(mom, isovalues, params, dx: float = 1.0, dy: float = 1.0, out_
 
 class Surrogate:
     """The network's parameters and Adam state on a device, trained and used
-    through the library's kernels."""
+    through the library's kernels.  Training is reproducible bit for bit (the
+    deterministic backward, element-wise Adam, a seeded shuffle), so a run
+    stopped at any step and resumed from ``checkpoint()`` ends with the same
+    parameters and Adam moments as the run that never stopped."""
 
     def __init__(self, init_params: dict, device="cuda"):
         self.params = torch.from_numpy(mlp_pack(init_params)).to(device)
@@ -157,30 +182,44 @@ class Surrogate:
         self.v = torch.zeros_like(self.params)
         self.grad = torch.empty_like(self.params)
         self.loss = torch.empty(1, dtype=torch.float32, device=device)
-        self.t = 0
+        self.t = 0          # Adam steps taken
+        self.step = 0       # position in the current fit's schedule (batches done)
+        self.ws = None
 
     def fit(self, feat, prior, target, epochs: int = 4, batch: int = 8192, lr: float = 3e-3,
-            lr_final: float = 3e-4, seed: int = 0):
+            lr_final: float = 3e-4, seed: int = 0, stop_after: int | None = None):
         """Minibatch Adam on (feat [n, 32] bf16, prior [n] fp32, target [n] fp32).  The rows are
         shuffled once (seeded); each epoch walks them in batches, the learning
-        rate decaying geometrically from lr to lr_final.  Returns the loss of
-        every epoch's last batch."""
+        rate decaying geometrically from lr to lr_final.  The schedule starts at
+        batch ``self.step`` (0 for a fresh network, the checkpoint's step for a
+        resumed one) and stops after ``stop_after`` batches of this call, or at
+        its end.  Returns the loss of every epoch's last batch done here."""
         n = feat.shape[0]
         g = torch.Generator(device=feat.device)
         g.manual_seed(int(seed))
         perm = torch.randperm(n, generator=g, device=feat.device)
         feat, prior, target = feat[perm].contiguous(), prior[perm].contiguous(), target[perm].contiguous()
-        steps = epochs * ((n + batch - 1) // batch)
+        per_epoch = (n + batch - 1) // batch
+        steps = epochs * per_epoch
         decay = (lr_final / lr) ** (1.0 / max(1, steps - 1))
-        losses, rate = [], lr
-        for _ in range(epochs):
-            for s in range(0, n, batch):
-                e = min(n, s + batch)
-                lcp_mlp_backward(self.params, feat[s:e], prior[s:e], target[s:e], self.grad, self.loss)
-                self.t += 1
-                lcp_adam_step(self.params, self.grad, self.m, self.v, self.t, rate)
-                rate *= decay
-            losses.append(float(self.loss.item()))  # loss of the epoch's last batch
+        rate = lr
+        for _ in range(self.step):  # the rate at the resumed step, by the same products as an unbroken run
+            rate *= decay
+        need = int(_lib().lcp_mlp_backward_workspace_bytes(min(n, batch)))
+        if self.ws is None or self.ws.numel() < need:
+            self.ws = torch.empty(need, dtype=torch.uint8, device=feat.device)
+        losses, done = [], 0
+        while self.step < steps and (stop_after is None or done < stop_after):
+            s = (self.step % per_epoch) * batch
+            e = min(n, s + batch)
+            lcp_mlp_backward_ws(self.params, feat[s:e], prior[s:e], target[s:e], self.grad, self.loss, self.ws)
+            self.t += 1
+            lcp_adam_step(self.params, self.grad, self.m, self.v, self.t, rate)
+            rate *= decay
+            self.step += 1
+            done += 1
+            if self.step % per_epoch == 0:
+                losses.append(float(self.loss.item()))  # loss of the epoch's last batch
         return losses
 
     def predict(self, feat, prior):
@@ -192,3 +231,28 @@ class Surrogate:
     def state(self) -> dict:
         return mlp_unpack(self.params.detach().cpu().numpy())
 
+    def checkpoint(self) -> dict:
+        """Everything training needs to continue: parameters, Adam moments and
+        step count, and the position in the schedule (host numpy arrays)."""
+        return {"params": self.params.detach().cpu().numpy().copy(), "m": self.m.detach().cpu().numpy().copy(),
+                "v": self.v.detach().cpu().numpy().copy(), "t": np.int64(self.t), "step": np.int64(self.step)}
+
+    def save(self, path: str):
+        np.savez(path, **self.checkpoint())
+
+    @classmethod
+    def from_checkpoint(cls, ck, device="cuda"):
+        """A network restored from ``checkpoint()`` (a dict, or the path of a ``save()`` file)."""
+        if isinstance(ck, str):
+            with np.load(ck) as z:
+                ck = {k: z[k] for k in z.files}
+        net = cls.__new__(cls)
+        net.params = torch.from_numpy(np.asarray(ck["params"], np.float32).copy()).to(device)
+        net.m = torch.from_numpy(np.asarray(ck["m"], np.float32).copy()).to(device)
+        net.v = torch.from_numpy(np.asarray(ck["v"], np.float32).copy()).to(device)
+        net.grad = torch.empty_like(net.params)
+        net.loss = torch.empty(1, dtype=torch.float32, device=device)
+        net.t = int(ck["t"])
+        net.step = int(ck["step"])
+        net.ws = None
+        return net
