@@ -219,6 +219,59 @@ def make_workload():
     return synth.fourier_ensemble(0, h=H, w=W, m=M, k=K)
 
 
+_POOL_U = _POOL_V = None
+
+
+def _pool_init(name_u, name_v, shape):
+    """Worker set-up of the all-cores oracle timing: attach the members."""
+    global _POOL_U, _POOL_V, _POOL_SHM
+    from multiprocessing import shared_memory
+
+    _POOL_SHM = (shared_memory.SharedMemory(name=name_u), shared_memory.SharedMemory(name=name_v))
+    _POOL_U = np.ndarray(shape, np.float32, buffer=_POOL_SHM[0].buf)
+    _POOL_V = np.ndarray(shape, np.float32, buffer=_POOL_SHM[1].buf)
+
+
+def _pool_band(task):
+    import oracle as O
+
+    j0, rows, iso = task
+    O.lcp_closed_form(_POOL_U[:, j0:j0 + rows], _POOL_V[:, j0:j0 + rows], 1.0, 1.0, iso)
+    return (rows - 1) * (_POOL_U.shape[2] - 1)
+
+
+def cpu_baseline_all_cores(d, budget_s=12.0, rows=61):
+    """The same oracle bands on every host core: one process per core (spawn
+    start method: this process already holds a CUDA context), the members in
+    shared memory, ~budget_s of wall time."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    u, v = np.ascontiguousarray(d["u"], np.float32), np.ascontiguousarray(d["v"], np.float32)
+    shm = [shared_memory.SharedMemory(create=True, size=u.nbytes) for _ in range(2)]
+    try:
+        np.ndarray(u.shape, np.float32, buffer=shm[0].buf)[:] = u
+        np.ndarray(v.shape, np.float32, buffer=shm[1].buf)[:] = v
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores, initializer=_pool_init, initargs=(shm[0].name, shm[1].name, u.shape)) as pool:
+            iso = np.asarray(d["isovalues"])
+            pool.map(_pool_band, [((n * 97) % (H - rows), rows, iso) for n in range(cores)])  # warm every worker
+            t0, cells, n = time.perf_counter(), 0, 0
+            while time.perf_counter() - t0 < budget_s:
+                tasks = [((k * 97) % (H - rows), rows, iso) for k in range(n, n + 4 * cores)]
+                cells += sum(pool.map(_pool_band, tasks))
+                n += len(tasks)
+            dt = time.perf_counter() - t0
+    finally:
+        for m in shm:
+            m.close()
+            m.unlink()
+    return {"value": cells / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} bands of {rows} rows x {W} cols x {M} members, K={K} (FP64 numpy, one process per core)",
+            "seconds": round(dt, 2)}
+
+
 def cpu_baseline(d, budget_s=12.0, rows=None):
     """Time the FP64 oracle, as it stands, on row bands of the workload."""
     import oracle as O
@@ -307,6 +360,49 @@ def mc_equal_error(lib, torch, u, v, iso, t_closed_s):
         out[f"S_star_{key}"] = round(s_star)
         out[f"t_mc_s_{key}"] = round(s_star * rate, 4)
         out[f"speedup_closed_vs_mc_{key}"] = round(s_star * rate / t_closed_s, 1)
+    # throughput of the estimator: vertex-samples per second (2 normal variates each)
+    out["vertex_samples_per_s"] = float(H * W / rate)
+
+    def confirm(uu, vv, st_, ref_, s_guess, tol, t_closed):
+        """Run MC at the fitted S (then 1.5x, at most three times) until its
+        max-abs error on interior cells is at most tol; the measured time."""
+        s_try = int(s_guess)
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            est, _ = lib.lcp_mc(iso, s_try, seed=777 + s_try, stats=st_)
+            e1.record()
+            torch.cuda.synchronize()
+            err = float((est[:, 1:-1, 1:-1].double() - ref_).abs().max())
+            if err <= tol:
+                break
+            s_try = int(s_try * 1.5)
+        t = e0.elapsed_time(e1) / 1e3
+        return {"S": s_try, "max_abs_err": round(err, 6), "t_mc_s": round(t, 4),
+                "t_closed_s": round(t_closed, 6), "speedup_closed_vs_mc": round(t / t_closed, 1), "met": err <= tol}
+
+    # 1e-2 on the full field, at the fitted S
+    out["confirmed_1e-2_full_field"] = confirm(u, v, st, ref, out["S_star_1e-2"], 1e-2, t_closed_s)
+    # 1e-3 on a 256 x 256 crop (its own grid for both estimators), at the S fitted on the crop
+    cu, cv = u[:, 200:456, 500:756].contiguous(), v[:, 200:456, 500:756].contiguous()
+    cst = lib.lcp_stats(cu, cv, 1)
+    ccl, _ = lib.lcp_fused(cu, cv, iso)
+    cref = ccl[:, 1:-1, 1:-1].double()
+    cs = []
+    for s_ in (1024, 4096, 16384):
+        est, _ = lib.lcp_mc(iso, s_, seed=99 + s_, stats=cst)
+        cs.append(float((est[:, 1:-1, 1:-1].double() - cref).abs().max()) * np.sqrt(s_))
+    s_crop = (float(np.median(cs)) / 1e-3) ** 2
+    for _ in range(3):
+        lib.lcp_fused(cu, cv, iso)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        lib.lcp_fused(cu, cv, iso)
+    e1.record()
+    torch.cuda.synchronize()
+    out["confirmed_1e-3_crop_256"] = confirm(cu, cv, cst, cref, s_crop, 1e-3, e0.elapsed_time(e1) / 20 / 1e3)
+    out["confirmed_1e-3_crop_256"]["S_fitted"] = round(s_crop)
     return out
 
 
@@ -399,7 +495,9 @@ def our_arm(args):
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
-        cpu = cpu_baseline(d)
+        cpu = cpu_baseline_all_cores(d)
+        serial = cpu_baseline(d)
+        cpu["serial"] = {k: serial[k] for k in ("value", "cores", "sample", "seconds")}
 
     if rank == 0:
         line = {
