@@ -824,6 +824,10 @@ def learned_arm(args):
                "mc_S_at_learned_rms": round(s_rms), "mc_S_at_learned_max": round(s_max),
                "t_mc_over_t_learned_at_equal_rms": round(s_rms * rate / ms_per_step, 1),
                "t_mc_over_t_learned_at_equal_max": round(s_max * rate / ms_per_step, 1),
+               # the stated target: equal max-abs error 1e-2 against the judge
+               "target_max_abs_1e-2": {"learned_meets": max_l <= 1e-2, "closed_form_meets": max_c <= 1e-2,
+                                       "mc_S": round((c_max / 1e-2) ** 2),
+                                       "mc_ms": round((c_max / 1e-2) ** 2 * rate, 3)},
                "train_s": round(t_train, 2), "train_final_loss": round(losses[-1], 6),
                "full_field_gpu_judge": {"exact_ms": round(exact_ms, 3),
                                         **{k: {"rms": round(a, 5), "max": round(b, 5)} for k, (a, b) in full.items()}}}
