@@ -633,8 +633,8 @@ __global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer
     OutT* const obase = reinterpret_cast<OutT*>(p.out);
     Off oo = (Off)p.kbase * plane + (Off)(a - 1) * (Off)Wc + (Off)i;  // row a - 1: advanced before the first store
     Off mo = MASK ? ((Off)p.kbase * (Off)Hc + (Off)(a - 1)) * (Off)p.n_words + (Off)wi : (Off)0;
-#pragma unroll 1
-    for (int jj = 0; jj <= kTR; ++jj) {  // vertex rows a .. e (at most kTR + 1); a rolled loop keeps the code small
+#pragma unroll(KX <= 4 ? 2 : 1)  // small code (measured: rolled best at K = 8, two rows per trip at K = 4)
+    for (int jj = 0; jj <= kTR; ++jj) {  // vertex rows a .. e (at most kTR + 1)
         const int j = a + jj;
         if (j > e) break;
         const RowRec C = R0;
