@@ -3,38 +3,38 @@
 // the LCP of every cell, Sec. 3.1 last paragraph).
 //
 // 1) stats_ws_kernel: a flat, fully coalesced stream over the member planes --
-//    each thread owns VEC consecutive vertices and keeps 16 independent
-//    16-byte loads in flight, the access pattern that runs near HBM peak.  Per
-//    vertex and component it stores one 16-byte record (x0, delta, var, 0):
+//    each thread owns VEC consecutive vertices of a chunk and keeps 16
+//    independent loads in flight, the access pattern that runs near HBM peak.
+//    Per vertex and component it stores one 16-byte record (x0, delta, var, 0):
 //    member 0, the FP32 mean of the values shifted by member 0, and the
 //    variance.  Member loads carry an L2 evict-first policy and the record
-//    stores evict-last, so the 32 bytes per vertex stay in the 129 MB L2.
-// 2) lcp_rows_kernel: a tile of 8 cell rows x 256 cell columns, one vertex
-//    column per thread, marching down the rows with a sliding register window
-//    (own column's u record, whose horizontal neighbours come by warp shuffle;
-//    v records of rows j-1, j, j+1), the next row always in flight.  Phase A:
-//    each thread forms the divergence Gaussian of its vertex and evaluates one
-//    erfc per isovalue into shared memory (the tile's extra right vertex is
-//    loaded by four lanes of the last warp, gathered by shuffle, and its
-//    isovalues shared out over the lanes).  Phase B: each thread forms its
-//    cell's horizontal products p_i p_{i+1}, q_i q_{i+1}, closes the cell with
-//    the previous row's products (kept in registers), stores it coalesced, and
-//    the warp ballots the mean-field crossing bits into whole mask words.  The
-//    kernel is compiled for exact isovalue counts 1, 2, 4, 8, 16, 32 (other K
-//    run as a sum of such passes), so the isovalue loop has no guards.
+//    stores evict-last, so the 32 bytes per vertex stay in the 129 MB L2.  The
+//    same pass clears the mean-field mask rows of its chunk.
+// 2) LCP from the records.  Up to 8 isovalues: lcp_warp_rows_kernel, where every
+//    warp marches down 8 cell rows of a 31-cell strip with a sliding register
+//    window (own u record, horizontal neighbours by warp shuffle; v records of
+//    rows j-1, j, j+1), the next row always in flight; each lane forms its
+//    vertex's divergence Gaussian and its (P(D<c), P(D>=c)) per isovalue, takes
+//    its right neighbour's by shuffle, closes its cell with the previous row's
+//    products, and the warp ORs the mean-field crossing bits into the mask
+//    words.  More isovalues: lcp_rows_kernel, a 256-column tile that shares a
+//    row's vertex values through shared memory (passes of up to 32).  Both are
+//    compiled for exact isovalue counts, so the isovalue loop has no guards.
 //
 // Overlap.  The statistics grid triggers its programmatic dependents as each
-// block starts and, after storing, counts itself into per-row-band counters in
-// the workspace (fence, then atomic add).  The LCP grid, launched as its
+// block starts and, after storing a chunk, counts it into per-row-band counters
+// in the workspace (fence, then atomic add).  The LCP grid, launched as its
 // programmatic dependent, therefore starts as soon as every statistics block
-// is resident (its last wave), and each LCP block waits -- bounded, with
-// backoff -- only for the statistics rows of its own band.  The wait cannot
-// deadlock: every block it waits for is already running.
+// is resident, and each LCP block waits -- bounded, with backoff -- only for
+// the statistics rows of its own band.  The wait cannot deadlock: every block
+// it waits for is already running.
 //
 // Grids whose records would not fit comfortably in L2 (a 96 MB budget) are
 // processed in bands of rows (records of the band plus one halo row on each
 // side, then its cells), so the workspace never spills to HBM; a smaller
-// workspace than lcp_fused_workspace_bytes reports gives smaller bands.
+// workspace than lcp_fused_workspace_bytes reports gives smaller bands.  With
+// several bands the statistics grid is persistent (3 blocks per SM), so that
+// the LCP grid runs beside each band's stream rather than after it.
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
@@ -152,8 +152,11 @@ struct StatsWsParams {
     float4* st;              // record planes: u at st, v at st + ps
     int64_t ps;              // plane stride in records
     int vecload;
-    uint32_t* dep;           // per LCP row band: statistics blocks completed
+    uint32_t* dep;           // per LCP row band: statistics chunks completed
     int H, r_begin, r_end, nby;
+    uint32_t* mzero;         // mask whose cell rows [r_begin, r_end) this pass clears (null: none)
+    int mK, mwords;          // its planes and words per row
+    int64_t mplane;          // words per plane
 };
 
 __device__ __forceinline__ void store_stats(const StatsWsParams& p, int64_t n, const float* x0, const float* s1,
@@ -178,8 +181,11 @@ __global__ void __launch_bounds__(kST, 4) stats_ws_kernel(const __grid_constant_
     // Every block of this grid is resident once all have executed this: the
     // dependent LCP grid may then launch and wait on the per-band counters.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int64_t n0 = p.n_begin + ((int64_t)blockIdx.x * kST + threadIdx.x) * VEC;
     const int M = p.M;
+    constexpr int sv = kST * VEC;  // vertices per chunk
+    const int64_t nchunks = (p.n_end - p.n_begin + sv - 1) / sv;
+    for (int64_t blk = blockIdx.x; blk < nchunks; blk += gridDim.x) {  // chunks in vertex order
+    const int64_t n0 = p.n_begin + (blk * kST + threadIdx.x) * VEC;
     if (n0 < p.n_end) {
         if (p.vecload && n0 + VEC <= p.n_end) {
             using L = SLoad<T, VEC>;
@@ -247,21 +253,30 @@ __global__ void __launch_bounds__(kST, 4) stats_ws_kernel(const __grid_constant_
             }
         }
     }
-    // publish: this block's statistics are stored; count it for every LCP row
-    // band whose rows it covers
+    const int64_t f0 = p.n_begin + blk * sv;  // this chunk's vertices [f0, f1]
+    const int64_t f1 = min(f0 + sv, p.n_end) - 1;
+    if (p.mzero) {  // clear the mask words of every cell row of this band whose first vertex is in the chunk
+        for (int64_t j = (f0 + p.W - 1) / p.W; j * p.W <= f1; ++j) {
+            if (j < p.r_begin || j >= p.r_end) continue;
+            for (int x = threadIdx.x; x < p.mK * p.mwords; x += kST) {
+                const int k = x / p.mwords, w = x - k * p.mwords;
+                p.mzero[(int64_t)k * p.mplane + j * p.mwords + w] = 0u;
+            }
+        }
+    }
+    // publish: this chunk's statistics (and mask rows) are stored; count it for
+    // every LCP row band whose rows it covers
     __syncthreads();
     if (threadIdx.x == 0 && p.dep) {
         __threadfence();
-        constexpr int sv = kST * VEC;
-        const int64_t f0 = p.n_begin + (int64_t)blockIdx.x * sv;
-        const int64_t f1 = min(f0 + sv, p.n_end) - 1;
         const int rs0 = (int)(f0 / p.W), rs1 = (int)(f1 / p.W);
         const int lo = max(0, (rs0 - 1 - p.r_begin) / kTR - 1), hi = min(p.nby - 1, (rs1 + 1 - p.r_begin) / kTR + 1);
         for (int by = lo; by <= hi; ++by) {
             int blo, bhi;
             band_blocks(p.n_begin, sv, p.W, p.H, p.r_begin, p.r_end, by, blo, bhi);
-            if ((int)blockIdx.x >= blo && (int)blockIdx.x <= bhi) atomicAdd(&p.dep[by], 1u);
+            if ((int)blk >= blo && (int)blk <= bhi) atomicAdd(&p.dep[by], 1u);
         }
+    }
     }
 }
 
@@ -553,76 +568,79 @@ __global__ void __launch_bounds__(kRT, KX <= 4 ? 3 : (KX <= 16 ? 2 : 1))
     }
 }
 
-// Barrier-free variant: every warp evaluates 32 cells on its own.  Lane l owns
-// vertex c0w + l; the right neighbour's (P(D<c), P(D>=c)) and class bits come
-// from lane l + 1 by shuffle, and for lane 31 from the warp's 33rd vertex,
-// whose four stencil records are loaded one per lane 0..3 and shared by
-// shuffle, and whose isovalues are evaluated one per lane (lane k: isovalue
-// k) and passed on by shuffle.  No shared memory, no barriers after the dependency wait;
-// 32-cell warps keep the mask words aligned.  KX <= 8 isovalues per pass.
-constexpr int kWT = 128;  // threads (4 warps = 128 cells) per block
+// Barrier-free variant: every warp evaluates a 31-cell strip on its own.  Lane l
+// owns vertex c0w + l (c0w = 31 x the warp's strip index); lanes 0..30 own the
+// cells [c0w, c0w + 31), and lane 31's vertex closes cell c0w + 30.  The right
+// neighbour's (P(D<c), P(D>=c)) and class bits come from lane l + 1 by shuffle,
+// so no vertex of a row is evaluated twice and no lane waits on another warp.
+// No shared memory, no barriers after the dependency wait.  A mask word (32
+// cells) straddles two warps, so each warp ORs its 31 bits into the word(s)
+// atomically; the words are cleared beforehand (by the statistics pass, row by
+// row, before it releases the row's band; or by the caller's stream).  KX <= 8
+// isovalues per pass.
+constexpr int kWT = 128;  // threads (4 warps) per block
+constexpr int kWC = 31;   // cells per warp
 
 template <int KX, bool MASK, typename OutT, bool IDX32>
-__global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer registers, more warps to hide L2
+__global__ void __launch_bounds__(kWT, 5)  // <= 102 registers: 20 warps per SM to hide the L2 latency
     lcp_warp_rows_kernel(const __grid_constant__ RowsParams p, const __grid_constant__ IsoParams iso) {
     // output and mask element offsets in 32 bits when the outputs fit (IDX32), else 64
     using Off = typename std::conditional<IDX32, uint32_t, int64_t>::type;
     static_assert(KX >= 1 && KX <= 8, "isovalues per pass");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int H = p.H, W = p.W, Hc = H - 1, Wc = W - 1;
-    const int c0w = blockIdx.x * kWT + warp * 32;
+    const int c0w = (blockIdx.x * (kWT / 32) + warp) * kWC;
     const int a = p.r_begin + blockIdx.y * kTR;
     if (a >= p.r_end) return;
     const int e = min(a + kTR, p.r_end);  // cells [a, e), vertex rows a..e
+    const int i = c0w + lane, ic = min(i, W - 1);
+    const bool ok = lane < kWC && i < Wc;
+    const int w0 = c0w >> 5, sh = c0w & 31;               // the strip starts at bit sh of mask word w0
+    const bool second_word = sh > 1 && w0 + 1 < p.n_words;  // bits sh .. sh + 30 reach word w0 + 1
     // wait (bounded) until the statistics rows this band reads are complete
     if (p.dep && wait_band(p, blockIdx.y)) {
-        fill_stalled<KX, MASK, OutT>(p, a, e, c0w + lane, c0w >> 5, lane == 0 && (c0w >> 5) < p.n_words);
+        // the records may be incomplete: NaN cells, and this strip's mask bits cleared
+        const int64_t plane = (int64_t)Hc * Wc, mplane = (int64_t)Hc * p.n_words;
+        OutT* o = reinterpret_cast<OutT*>(p.out);
+        const OutT nan = to_out<OutT>(__int_as_float(0x7FC00000));
+        const uint32_t bits = c0w < Wc ? (uint32_t)((1ull << min(kWC, Wc - c0w)) - 1) : 0u;
+        for (int j = a; j < e; ++j)
+            for (int k = 0; k < KX; ++k) {
+                if (ok) o[(int64_t)(p.kbase + k) * plane + (int64_t)j * Wc + i] = nan;
+                if (MASK && lane == 0 && bits) {
+                    uint32_t* m = p.mask + (int64_t)(p.kbase + k) * mplane + (int64_t)j * p.n_words + w0;
+                    atomicAnd(m, ~(bits << sh));
+                    if (second_word) atomicAnd(m + 1, ~(bits >> (32 - sh)));
+                }
+            }
         return;
     }
     // the next isovalue pass may launch once every block of this grid is past its wait
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (c0w >= Wc) return;  // whole warp beyond the last cell (uniform per warp)
-    const int i = c0w + lane, ic = min(i, W - 1);
-    const bool ok = i < Wc;
     const bool osx = ic == 0 || ic == W - 1;
     const float sx = osx ? p.sp.sx1 : p.sp.sx2, sxq = osx ? p.sp.sx1q : p.sp.sx2q;
     const double dsx = osx ? p.dsx1 : p.dsx2;
     const bool edge_lane = lane == 0 || lane == 31;
-    const int iedge = lane == 0 ? max(ic - 1, 0) : min(ic + 1, W - 1);
-    const int ix = min(c0w + 32, W - 1);  // the warp's 33rd vertex
-    const bool osxx = ix == 0 || ix == W - 1;
-    const float sx_x = osxx ? p.sp.sx1 : p.sp.sx2, sxq_x = osxx ? p.sp.sx1q : p.sp.sx2q;
-    const double dsx_x = osxx ? p.dsx1 : p.dsx2;
-    const int ixl = max(ix - 1, 0), ixr = min(ix + 1, W - 1);
-    const int wi = c0w >> 5;
+    const int iedge = lane == 0 ? max(ic - 1, 0) : min(ic + 1, W - 1);  // u neighbour beyond the warp
     float c[KX];
 #pragma unroll
     for (int k = 0; k < KX; ++k) c[k] = iso.c[k];
-    float cl = 0.0f;  // this lane's isovalue for the 33rd vertex
-#pragma unroll
-    for (int k = 0; k < KX; ++k)
-        if (k == lane) cl = c[k];
 
     const float4* ubase = p.st - (int64_t)p.row0 * W;  // u records of grid row j at ubase + j W
     const float4* vbase = ubase + p.ps;
     auto urow = [&](int j) { return ubase + (int64_t)j * W; };
     auto vrow = [&](int j) { return vbase + (int64_t)j * W; };
-    // the records one vertex row needs beyond the sliding v window: own u, the warp-edge u neighbour,
-    // the v record two rows down (the window's next VP), and one record of the 33rd vertex's stencil
-    // per lane 0..3 (u at ix-1, u at ix+1, v at (j-1, ix), v at (j+1, ix))
+    // the records one vertex row needs beyond the sliding v window: own u, the warp-edge
+    // u neighbour, and the v record one row down (the window's next VP)
     struct RowRec {
-        float4 U, UE, VN, X;
+        float4 U, UE, VN;
     };
     auto load_row = [&](int j) {
         RowRec r;
         r.U = ld_rec(urow(j) + ic);
         r.UE = edge_lane ? ld_rec(urow(j) + iedge) : make_float4(0.f, 0.f, 0.f, 0.f);
         r.VN = ld_rec(vrow(min(j + 1, H - 1)) + ic);
-        r.X = lane == 0 ? ld_rec(urow(j) + ixl)
-                        : lane == 1 ? ld_rec(urow(j) + ixr)
-                                    : lane == 2 ? ld_rec(vrow(max(j - 1, 0)) + ix)
-                                                : lane == 3 ? ld_rec(vrow(min(j + 1, H - 1)) + ix)
-                                                            : make_float4(0.f, 0.f, 0.f, 0.f);
         return r;
     };
     float4 VM = ld_rec(vrow(max(a - 1, 0)) + ic), V0 = ld_rec(vrow(a) + ic);
@@ -632,7 +650,7 @@ __global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer
     const Off plane = (Off)Hc * (Off)Wc, mplane = (Off)Hc * (Off)p.n_words;
     OutT* const obase = reinterpret_cast<OutT*>(p.out);
     Off oo = (Off)p.kbase * plane + (Off)(a - 1) * (Off)Wc + (Off)i;  // row a - 1: advanced before the first store
-    Off mo = MASK ? ((Off)p.kbase * (Off)Hc + (Off)(a - 1)) * (Off)p.n_words + (Off)wi : (Off)0;
+    Off mo = MASK ? ((Off)p.kbase * (Off)Hc + (Off)(a - 1)) * (Off)p.n_words + (Off)w0 : (Off)0;
 #pragma unroll(KX <= 4 ? 2 : 1)  // small code (measured: rolled best at K = 8, two rows per trip at K = 4)
     for (int jj = 0; jj <= kTR; ++jj) {  // vertex rows a .. e (at most kTR + 1)
         const int j = a + jj;
@@ -655,21 +673,14 @@ __global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer
         const float4 Vhi = j < H - 1 ? VP : V0;
         float mu = fmaf((R.x - L.x) + (R.y - L.y), sx, ((Vhi.x - Vlo.x) + (Vhi.y - Vlo.y)) * sy);
         const float var = fmaf(R.z + L.z, sxq, (Vhi.z + Vlo.z) * syq);
-        // the 33rd vertex (every lane, from lanes 0..3's records); (ixl, ixr) and the clamped rows
-        // already are the one-sided stencil at the edges
-        const float4 XLc = shfl_rec(C.X, 0), XRc = shfl_rec(C.X, 1), XDc = shfl_rec(C.X, 2), XUc = shfl_rec(C.X, 3);
-        float mux = fmaf((XRc.x - XLc.x) + (XRc.y - XLc.y), sx_x, ((XUc.x - XDc.x) + (XUc.y - XDc.y)) * sy);
-        const float varx = fmaf(XRc.z + XLc.z, sxq_x, (XUc.z + XDc.z) * syq);
         const bool zero = var == 0.0f;
-        const float s = rsqrtf(2.0f * var), sxv = rsqrtf(2.0f * varx);
+        const float s = rsqrtf(2.0f * var);
         // member-0 differences across the stencil of more than 16 sigma: the mean again in FP64, as mu + lo
-        float lo = 0.0f, lox = 0.0f;
+        float lo = 0.0f;
         const bool big = !(fmaf(fabsf(R.x - L.x), sx, fabsf(Vhi.x - Vlo.x) * sy) * s <= kExactZ);
-        const bool bigx = !(fmaf(fabsf(XRc.x - XLc.x), sx_x, fabsf(XUc.x - XDc.x) * sy) * sxv <= kExactZ);
-        if (__any_sync(0xFFFFFFFFu, big || bigx)) {
+        if (__any_sync(0xFFFFFFFFu, big)) {
             const double dsy = osy ? p.dsy1 : p.dsy2;
             if (big) lo = mu_fp64(mu, L, R, Vlo, Vhi, dsx, dsy);
-            if (bigx) lox = mu_fp64(mux, XLc, XRc, XDc, XUc, dsx_x, dsy);
         }
         float2 pq[KX];
         uint32_t b = 0;
@@ -688,12 +699,8 @@ __global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer
                 b |= ((uint32_t)b0 << k) | ((uint32_t)b1 << (k + 1));
             }
         }
-        const float dx_ = (mux - cl) + lox;
-        const bool belowx = dx_ < 0.0f;
-        const float2 pqx = vertex_pq_d(dx_, sxv, varx == 0.0f, belowx);
-        const uint32_t bx = __ballot_sync(0xFFFFFFFFu, lane < KX && belowx);
-        uint32_t bn = __shfl_down_sync(0xFFFFFFFFu, b, 1);
-        if (lane == 31) bn = bx;
+        const uint32_t bn = __shfl_down_sync(0xFFFFFFFFu, b, 1);  // lane 31 owns no cell
+        // bit k: the cell's four vertices are not all on one side of c_k
         const uint32_t cross = ok ? ((b_prev | bn_prev | b | bn) & ~(b_prev & bn_prev & b & bn)) : 0u;
         if (j > a) {
             oo += (Off)Wc;
@@ -701,16 +708,19 @@ __global__ void __launch_bounds__(kWT, KX <= 4 ? 5 : 4)  // few isovalues: fewer
         }
 #pragma unroll
         for (int k = 0; k < KX; ++k) {
-            float2 nb = make_float2(__shfl_down_sync(0xFFFFFFFFu, pq[k].x, 1), __shfl_down_sync(0xFFFFFFFFu, pq[k].y, 1));
-            const float2 xk = make_float2(__shfl_sync(0xFFFFFFFFu, pqx.x, k), __shfl_sync(0xFFFFFFFFu, pqx.y, k));
-            if (lane == 31) nb = xk;
+            const float2 nb = make_float2(__shfl_down_sync(0xFFFFFFFFu, pq[k].x, 1),
+                                          __shfl_down_sync(0xFFFFFFFFu, pq[k].y, 1));
             const float2 h = __fmul2_rn(pq[k], nb);  // (p_i p_i+1, q_i q_i+1) of this vertex row
             if (j > a) {
                 const float lcp = fmaf(-qh_prev[k], h.y, fmaf(-ph_prev[k], h.x, 1.0f));
                 if (ok) obase[oo + (Off)k * plane] = to_out<OutT>(clamp01_nan(lcp));
                 if (MASK) {
                     const uint32_t word = __ballot_sync(0xFFFFFFFFu, (cross >> k) & 1u);
-                    if (lane == 0 && wi < p.n_words) p.mask[mo + (Off)k * mplane] = word;
+                    if (lane == 0 && word) {
+                        uint32_t* m = p.mask + (mo + (Off)k * mplane);
+                        atomicOr(m, word << sh);
+                        if (second_word && (word >> (32 - sh))) atomicOr(m + 1, word >> (32 - sh));
+                    }
                 }
             }
             ph_prev[k] = h.x;
@@ -802,8 +812,9 @@ lcp_status launch_rows_k(const RowsParams& p, const IsoParams& ip, cudaStream_t 
 template <int KX, bool MASK, typename OutT>
 lcp_status launch_warp_rows_k(const RowsParams& p, const IsoParams& ip, cudaStream_t st, bool pdl) {
     const int rows = p.r_end - p.r_begin;
+    const int strips = (p.W - 1 + kWC - 1) / kWC;  // 31-cell warp strips per cell row
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((p.W - 1 + kWT - 1) / kWT, (rows + kTR - 1) / kTR);
+    cfg.gridDim = dim3((strips + kWT / 32 - 1) / (kWT / 32), (rows + kTR - 1) / kTR);
     cfg.blockDim = dim3(kWT);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
@@ -854,11 +865,24 @@ lcp_status launch_rows_chunk(const RowsParams& p, const IsoParams& ip, cudaStrea
 
 // Isovalues in passes whose sizes are the binary digits of K (largest first,
 // at most 32 each): every pass runs a kernel specialised for its exact count.
+// The warp kernel (K <= 8) ORs its mask bits into cleared words: unless the
+// statistics pass of this call clears them (mask_cleared), the mask of cell rows
+// [r_begin, r_end) is cleared here first, on the stream.
 template <typename OutT>
-lcp_status launch_rows(const RowsParams& p0, const float* iso, int K, cudaStream_t st, bool pdl = true) {
+lcp_status launch_rows(const RowsParams& p0, const float* iso, int K, cudaStream_t st, bool pdl = true,
+                       bool mask_cleared = false) {
     RowsParams p = p0;
     int kb = 0;
     const bool warp_rows = K <= 8;
+    if (warp_rows && p.mask && !mask_cleared) {
+        const int64_t mplane = (int64_t)(p.H - 1) * p.n_words;
+        const int64_t rows = (int64_t)(p.r_end - p.r_begin) * p.n_words;
+        const bool whole = rows == mplane;  // every plane whole: one contiguous clear
+        for (int k = 0; k < (whole ? 1 : K); ++k)
+            if (cudaMemsetAsync(p.mask + (int64_t)k * mplane + (int64_t)p.r_begin * p.n_words, 0,
+                                (size_t)(whole ? K * mplane : rows) * 4, st) != cudaSuccess)
+                return fail(LCP_ERR_CUDA, "lcp_fused_ws: mask clear failed");
+    }
     const int max_chunk = warp_rows ? 8 : kMaxKPass;
     while (kb < K) {
         int chunk = max_chunk;
@@ -911,8 +935,20 @@ lcp_status run(const void* u, const void* v, int M, int H, int W, int64_t stride
         sp.r_begin = r0;
         sp.r_end = r1;
         sp.nby = nby;
+        // the warp LCP kernel (K <= 8) ORs its mask bits into words this pass clears
+        sp.mzero = (mask && K <= 8) ? mask : nullptr;
+        sp.mK = K;
+        sp.mwords = (W - 1 + 31) / 32;
+        sp.mplane = (int64_t)Hc * sp.mwords;
         const int64_t groups = (sp.n_end - sp.n_begin + VEC - 1) / VEC;
-        stats_ws_kernel<T, VEC><<<(unsigned)((groups + kST - 1) / kST), kST, 0, st>>>(sp);
+        int64_t grid = (groups + kST - 1) / kST;  // one chunk per block
+        // Several bands: a persistent grid of 3 blocks per SM (chunks in vertex order),
+        // so that every block is resident at once, the dependent LCP grid launches
+        // at the start and its blocks run beside the stream on the SM space left
+        // over, instead of after the band's last wave (measured: 8192^2 bf16 K = 4,
+        // 2.68 -> 2.54 ms; a single band is faster with one chunk per block).
+        if (L.band_rows < Hc) grid = std::min<int64_t>(grid, (int64_t)num_sms() * 3);
+        stats_ws_kernel<T, VEC><<<(unsigned)grid, kST, 0, st>>>(sp);
         lcp_status s = check_launch("lcp_fused_ws (statistics)");
         if (s != LCP_OK) return s;
         RowsParams rp;
@@ -932,7 +968,8 @@ lcp_status run(const void* u, const void* v, int M, int H, int W, int64_t stride
         rp.n_begin = sp.n_begin;
         rp.sv = kST * VEC;
         rp.budget = wait_budget_cycles();
-        s = out_dtype == LCP_F16 ? launch_rows<__half>(rp, iso, K, st) : launch_rows<float>(rp, iso, K, st);
+        s = out_dtype == LCP_F16 ? launch_rows<__half>(rp, iso, K, st, true, true)
+                                 : launch_rows<float>(rp, iso, K, st, true, true);
         if (s != LCP_OK) return s;
     }
     return LCP_OK;
