@@ -706,6 +706,7 @@ __global__ void __launch_bounds__(kWT, 5)  // <= 102 registers: 20 warps per SM 
             oo += (Off)Wc;
             if (MASK) mo += (Off)p.n_words;
         }
+        uint32_t word = 0;  // lane k < KX: the strip's crossing bits for isovalue k
 #pragma unroll
         for (int k = 0; k < KX; ++k) {
             const float2 nb = make_float2(__shfl_down_sync(0xFFFFFFFFu, pq[k].x, 1),
@@ -715,16 +716,18 @@ __global__ void __launch_bounds__(kWT, 5)  // <= 102 registers: 20 warps per SM 
                 const float lcp = fmaf(-qh_prev[k], h.y, fmaf(-ph_prev[k], h.x, 1.0f));
                 if (ok) obase[oo + (Off)k * plane] = to_out<OutT>(clamp01_nan(lcp));
                 if (MASK) {
-                    const uint32_t word = __ballot_sync(0xFFFFFFFFu, (cross >> k) & 1u);
-                    if (lane == 0 && word) {
-                        uint32_t* m = p.mask + (mo + (Off)k * mplane);
-                        atomicOr(m, word << sh);
-                        if (second_word && (word >> (32 - sh))) atomicOr(m + 1, word >> (32 - sh));
-                    }
+                    const uint32_t wk = __ballot_sync(0xFFFFFFFFu, (cross >> k) & 1u);
+                    word = lane == k ? wk : word;
                 }
             }
             ph_prev[k] = h.x;
             qh_prev[k] = h.y;
+        }
+        // one divergent section per row: lane k ORs isovalue k's bits into its word(s)
+        if (MASK && j > a && lane < KX && word) {
+            uint32_t* m = p.mask + (mo + (Off)lane * mplane);
+            atomicOr(m, word << sh);
+            if (second_word && (word >> (32 - sh))) atomicOr(m + 1, word >> (32 - sh));
         }
         b_prev = b;
         bn_prev = bn;
