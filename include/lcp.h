@@ -369,8 +369,9 @@ lcp_status lcp_mlp_forward(const float* params, const void* feat, const float* p
  * (1/n) sum_r (network(feat[r], prior[r]) - target[r])^2 with respect to every
  * parameter, written to grad (fp32 [LCP_MLP_NPARAMS], device; overwritten,
  * padding and the zero columns of W1 get 0).  loss (device fp32 scalar, or
- * NULL) receives the loss itself.  Weight gradients are contractions over the
- * rows on the tensor cores, FP32-accumulated.
+ * NULL) receives the loss itself.  Forward and backward products and the
+ * weight gradients (contractions over the rows) run as tcgen05.mma on the
+ * tensor cores, BF16 operands, FP32-accumulated in tensor memory.
  */
 lcp_status lcp_mlp_backward(const float* params, const void* feat, const float* prior, const float* target,
                             int64_t n, float* grad, float* loss, lcp_stream_t stream);
@@ -383,8 +384,8 @@ lcp_status lcp_mlp_backward(const float* params, const void* feat, const float* 
  * in CTA order.  Training with it (and the element-wise Adam step) is
  * reproducible, so a run resumed from a checkpoint continues exactly as the
  * uninterrupted run.  workspace: device, 16-byte aligned, at least
- * lcp_mlp_backward_workspace_bytes(n) bytes (about 25 KB per CTA, at most
- * two CTAs per SM); grad and loss are overwritten.  The paper has no
+ * lcp_mlp_backward_workspace_bytes(n) bytes (about 25 KB per CTA, one CTA per
+ * SM at most); grad and loss are overwritten.  The paper has no
  * counterpart (the surrogate is this library's addition).
  */
 size_t lcp_mlp_backward_workspace_bytes(int64_t n);

@@ -1,16 +1,14 @@
 // Learned surrogate: moments of the members, cumulants of the vertex
 // divergence under the empirical model, per-cell features, and a
-// 17 -> 64 -> 64 -> 1 network trained and evaluated on the tensor cores
-// (mma.sync m16n8k16, BF16 operands, FP32 accumulation).
-//
-// Register layouts of mma.sync.m16n8k16 (gid = lane / 4, tig = lane % 4):
-//   A (16 x 16, row-major):  a0 = A[gid][2 tig .. +1],     a1 = A[gid+8][2 tig ..],
-//                            a2 = A[gid][8 + 2 tig ..],    a3 = A[gid+8][8 + 2 tig ..]
-//   B (16 x 8, k x n):       b0 = B[2 tig .. +1][gid],     b1 = B[8 + 2 tig .. +1][gid]
-//   C (16 x 8, fp32):        c0, c1 = C[gid][2 tig .. +1], c2, c3 = C[gid+8][2 tig .. +1]
-// so the C fragments of two adjacent 8-column tiles are exactly the A fragment
-// of the next layer's 16-wide k-step (no shared-memory round trip between
-// layers).
+// 17 -> 64 -> 64 -> 1 network trained and evaluated on the 5th-generation
+// tensor cores: tcgen05.mma with BF16 operands in shared memory (canonical
+// K-major layout, no swizzle), FP32 accumulators in tensor memory read back
+// with tcgen05.ld, one thread issuing each layer's MMAs and committing them to
+// an mbarrier.  Inference (section 4) evaluates 128 cells per tile from the
+// moments; training (section 5) runs the forward pass, the backward pass and
+// the weight gradients of 128 feature rows per tile, the gradients as one more
+// contraction over the rows accumulated in tensor memory.
+
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -25,8 +23,6 @@ namespace {
 constexpr int kHid = 64;
 constexpr int kFS = LCP_MLP_FEAT_STRIDE;  // 32 bf16 per feature row
 constexpr int kOffW1 = 0, kOffB1 = 2048, kOffW2 = 2112, kOffB2 = 6208, kOffW3 = 6272, kOffB3 = 6336;
-constexpr int kW1S = 40;  // shared-memory row strides (bf16) chosen so that fragment loads hit 32 banks
-constexpr int kW2S = 72;
 
 // ---- 1. moments ---------------------------------------------------------------
 // Shifted power sums about member 0, then the central moments by the binomial
@@ -219,31 +215,13 @@ __global__ void __launch_bounds__(256) features_kernel(const float4* __restrict_
     }
 }
 
-// ---- 3. tensor-core building blocks -------------------------------------------
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
+// ---- 3. shared helpers --------------------------------------------------------
+constexpr int kMT = 128;           // threads per CTA of the network kernels (4 warps; one row or cell per thread)
+constexpr int kIR = 4, kIC = 32;   // inference CTA: 4 cell rows x 32 cell columns
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-
-// Four 8x8 bf16 matrices; lane l supplies the row address of matrix l / 8.
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_addr(p)));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_addr(p)));
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&h);
@@ -258,204 +236,7 @@ __device__ __forceinline__ float tanh_fast(float x) {
 }
 __device__ __forceinline__ float sigmoid(float z) { return 1.0f / (1.0f + __expf(-z)); }
 
-// Network weights in shared memory, BF16 operands and FP32 vectors.
-struct NetSmem {
-    __align__(16) __nv_bfloat16 W1[kHid * kW1S];  // [n][k]
-    __align__(16) __nv_bfloat16 W2[kHid * kW2S];  // [n][k]
-    __align__(16) float b1[kHid];
-    float b2[kHid], w3[kHid];
-    float b3;
-};
-
-__device__ void load_net(const float* __restrict__ prm, NetSmem& s, __nv_bfloat16* W2t /* [k][n], or null */) {
-    for (int q = threadIdx.x; q < kHid * kFS; q += blockDim.x) {
-        const int n = q / kFS, k = q - n * kFS;
-        s.W1[n * kW1S + k] = __float2bfloat16_rn(k < 17 ? prm[kOffW1 + q] : 0.f);
-    }
-    for (int q = threadIdx.x; q < kHid * kHid; q += blockDim.x) {
-        const int n = q >> 6, k = q & 63;
-        const __nv_bfloat16 w = __float2bfloat16_rn(prm[kOffW2 + q]);
-        s.W2[n * kW2S + k] = w;
-        if (W2t) W2t[k * kW2S + n] = w;
-    }
-    for (int q = threadIdx.x; q < kHid; q += blockDim.x) {
-        s.b1[q] = prm[kOffB1 + q];
-        s.b2[q] = prm[kOffB2 + q];
-        s.w3[q] = prm[kOffW3 + q];
-    }
-    if (threadIdx.x == 0) s.b3 = prm[kOffB3];
-}
-
-// One warp, 16 rows: layers 1 and 2 from the A fragments of the input (two
-// 16-feature k-steps).  Leaves h1 as bf16 A fragments (four 16-unit k-steps)
-// and h2 in C-fragment layout (fp32).
-__device__ __forceinline__ void forward16(const NetSmem& s, const uint32_t (&x)[2][4], uint32_t (&h1)[4][4],
-                                          float (&h2)[8][4], int gid, int tig) {
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const float bl = s.b1[8 * nt + 2 * tig], bh = s.b1[8 * nt + 2 * tig + 1];
-        acc[nt][0] = bl; acc[nt][1] = bh; acc[nt][2] = bl; acc[nt][3] = bh;
-    }
-#pragma unroll
-    for (int ks = 0; ks < 2; ++ks)
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const __nv_bfloat16* w = s.W1 + (8 * nt + gid) * kW1S + 16 * ks + 2 * tig;
-            mma16816(acc[nt], x[ks], *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
-        }
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-        const int a = 2 * ks, b = 2 * ks + 1;
-        h1[ks][0] = pack_bf16(tanh_fast(acc[a][0]), tanh_fast(acc[a][1]));
-        h1[ks][1] = pack_bf16(tanh_fast(acc[a][2]), tanh_fast(acc[a][3]));
-        h1[ks][2] = pack_bf16(tanh_fast(acc[b][0]), tanh_fast(acc[b][1]));
-        h1[ks][3] = pack_bf16(tanh_fast(acc[b][2]), tanh_fast(acc[b][3]));
-    }
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const float bl = s.b2[8 * nt + 2 * tig], bh = s.b2[8 * nt + 2 * tig + 1];
-        h2[nt][0] = bl; h2[nt][1] = bh; h2[nt][2] = bl; h2[nt][3] = bh;
-    }
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks)
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const __nv_bfloat16* w = s.W2 + (8 * nt + gid) * kW2S + 16 * ks + 2 * tig;
-            mma16816(h2[nt], h1[ks], *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
-        }
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) h2[nt][e] = tanh_fast(h2[nt][e]);
-}
-
-// Output pre-activation of rows gid and gid + 8 (complete in all four lanes of the group).
-__device__ __forceinline__ float2 output16(const NetSmem& s, const float (&h2)[8][4], int tig) {
-    float lo = 0.f, hi = 0.f;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const float w0 = s.w3[8 * nt + 2 * tig], w1 = s.w3[8 * nt + 2 * tig + 1];
-        lo = fmaf(h2[nt][0], w0, fmaf(h2[nt][1], w1, lo));
-        hi = fmaf(h2[nt][2], w0, fmaf(h2[nt][3], w1, hi));
-    }
-    lo += __shfl_xor_sync(0xFFFFFFFFu, lo, 1);
-    hi += __shfl_xor_sync(0xFFFFFFFFu, hi, 1);
-    lo += __shfl_xor_sync(0xFFFFFFFFu, lo, 2);
-    hi += __shfl_xor_sync(0xFFFFFFFFu, hi, 2);
-    return make_float2(lo + s.b3, hi + s.b3);
-}
-
-// A fragments of a 16-row x 32-feature tile held row-major in shared memory
-// (row stride kW1S bf16): matrices (rows 0-7 | 8-15) x (k 0-7 | 8-15) per k-step.
-__device__ __forceinline__ void load_x_frags(const __nv_bfloat16* tile, uint32_t (&x)[2][4], int lane) {
-    const int r = (lane & 7) + ((lane >> 3) & 1) * 8, c = (lane >> 4) * 8;
-#pragma unroll
-    for (int ks = 0; ks < 2; ++ks) ldsm_x4(x[ks], tile + r * kW1S + 16 * ks + c);
-}
-
-// ---- 4. forward over feature rows ---------------------------------------------
-constexpr int kMT = 128;  // threads per CTA of the network kernels (4 warps)
-
-__global__ void __launch_bounds__(kMT) mlp_forward_kernel(const float* __restrict__ prm,
-                                                         const __nv_bfloat16* __restrict__ feat,
-                                                         const float* __restrict__ prior, int64_t n,
-                                                         float* __restrict__ y) {
-    __shared__ NetSmem s;
-    __shared__ __align__(16) __nv_bfloat16 xs[kMT / 32][16 * kW1S];
-    load_net(prm, s, nullptr);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
-    __nv_bfloat16* tile = xs[warp];
-    for (int64_t r0 = ((int64_t)blockIdx.x * (kMT / 32) + warp) * 16; r0 < n;
-         r0 += (int64_t)gridDim.x * (kMT / 32) * 16) {
-        // stage 16 rows (64 B each): lane covers half a row
-        {
-            const int r = lane >> 1, h = lane & 1;
-            uint4 a = make_uint4(0, 0, 0, 0), b = a;
-            if (r0 + r < n) {
-                const uint4* src = reinterpret_cast<const uint4*>(feat + (r0 + r) * kFS) + 2 * h;
-                a = __ldg(src);
-                b = __ldg(src + 1);
-            }
-            uint4* dst = reinterpret_cast<uint4*>(tile + r * kW1S + 16 * h);
-            dst[0] = a;
-            dst[1] = b;
-        }
-        __syncwarp();
-        uint32_t x[2][4], h1[4][4];
-        float h2[8][4];
-        load_x_frags(tile, x, lane);
-        forward16(s, x, h1, h2, gid, tig);
-        const float2 z = output16(s, h2, tig);
-        if (tig == 0) {
-            if (r0 + gid < n) y[r0 + gid] = sigmoid(z.x + (prior ? __ldg(prior + r0 + gid) : 0.f));
-            if (r0 + gid + 8 < n) y[r0 + gid + 8] = sigmoid(z.y + (prior ? __ldg(prior + r0 + gid + 8) : 0.f));
-        }
-        __syncwarp();
-    }
-}
-
-// ---- 5. fused inference from moments ------------------------------------------
-// CTA: 4 cell rows x 32 cell columns, one warp per cell row, one lane per cell.
-// The cumulants of the tile's 5 x 33 vertices are computed once into shared
-// memory; per isovalue each lane writes its cell's feature row, and the warp
-// evaluates its 32 rows as two 16-row tensor-core tiles.
-constexpr int kIR = 4, kIC = 32;
-
-template <typename OutT>
-__global__ void __launch_bounds__(kMT) mlp_infer_kernel(const float4* __restrict__ mom, int H, int W, Spacing sp,
-                                                       const __grid_constant__ IsoParams iso,
-                                                       const float* __restrict__ prm, OutT* __restrict__ out) {
-    __shared__ NetSmem s;
-    __shared__ float4 kap[(kIR + 1) * (kIC + 1)];
-    __shared__ __align__(16) __nv_bfloat16 xs[kMT / 32][32 * kW1S];
-    load_net(prm, s, nullptr);
-    const int Hc = H - 1, Wc = W - 1;
-    const int a = blockIdx.y * kIR, c0 = blockIdx.x * kIC;
-    const int64_t n_vert = (int64_t)H * W;
-    for (int q = threadIdx.x; q < (kIR + 1) * (kIC + 1); q += blockDim.x) {
-        const int rr = q / (kIC + 1), cc = q - rr * (kIC + 1);
-        const int j = min(a + rr, H - 1), i = min(c0 + cc, W - 1);
-        kap[q] = vertex_cumulants(mom, mom + n_vert, H, W, j, i, sp);
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
-    const int j = a + warp, i = c0 + lane;
-    const bool ok = j < Hc && i < Wc;
-    float4 k4[4];
-    k4[0] = kap[warp * (kIC + 1) + lane];
-    k4[1] = kap[warp * (kIC + 1) + lane + 1];
-    k4[2] = kap[(warp + 1) * (kIC + 1) + lane];
-    k4[3] = kap[(warp + 1) * (kIC + 1) + lane + 1];
-    const CellPart part = cell_part(k4);
-    __nv_bfloat16* tile = xs[warp];
-    const int64_t plane = (int64_t)Hc * Wc;
-    for (int q = 0; q < iso.K; ++q) {
-        const float pr = cell_features(part, iso.c[q], tile + lane * kW1S);
-        __syncwarp();
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            uint32_t x[2][4], h1[4][4];
-            float h2[8][4];
-            load_x_frags(tile + 16 * mt * kW1S, x, lane);
-            forward16(s, x, h1, h2, gid, tig);
-            const float2 z = output16(s, h2, tig);
-            const float plo = __shfl_sync(0xFFFFFFFFu, pr, 16 * mt + gid);
-            const float phi = __shfl_sync(0xFFFFFFFFu, pr, 16 * mt + gid + 8);
-            if (tig == 0 && j < Hc) {
-                const int i0 = c0 + 16 * mt + gid;
-                OutT* o = out + (int64_t)q * plane + (int64_t)j * Wc;
-                if (i0 < Wc) o[i0] = to_out<OutT>(sigmoid(z.x + plo));
-                if (i0 + 8 < Wc) o[i0 + 8] = to_out<OutT>(sigmoid(z.y + phi));
-            }
-        }
-        __syncwarp();
-    }
-    (void)ok;
-}
-
-// ---- 5b. fused inference on the 5th-generation tensor cores (tcgen05) ---------
+// ---- 4. fused inference on the 5th-generation tensor cores (tcgen05) ----------
 // Per CTA a block of 4 x 32 cells, as above; per isovalue its 128 feature rows
 // form one M = 128 tile.  Each thread owns one row (= one TMEM lane): it writes
 // the row's features into shared memory in the canonical K-major layout
@@ -505,11 +286,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 
 constexpr uint32_t kIdescM128N64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate,
+                                       uint32_t idesc = kIdescM128N64) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdescM128N64), "r"(accumulate));
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 __device__ __forceinline__ void tc_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
@@ -699,259 +481,343 @@ __global__ void __launch_bounds__(kMT, kTcCtasPerSm) mlp_infer_tc_kernel(const f
 
 constexpr size_t kTcSmemBytes = sizeof(TcSmem) + 1024;
 
-// ---- 6. backward: gradient of the mean squared error ---------------------------
-// Per iteration a CTA takes 64 rows (16 per warp).  Each warp runs the forward
-// pass, the output and hidden-layer deltas (dA1 = dZ2 W2^T on the tensor cores,
-// dZ2 in registers as its A fragments), and stages X, h1, dZ1, dZ2 (bf16) in
-// shared memory; the CTA then accumulates the weight gradients
-// dW2 = dZ2^T h1 and dW1 = dZ1^T X as contractions over the 64 rows
-// (ldmatrix .trans supplies the transposed operands), in registers across
-// iterations, and adds them to the output once at the end.
-struct BwdSmem {
-    NetSmem net;
-    __align__(16) __nv_bfloat16 W2t[kHid * kW2S];  // [k][n] = W2[n][k]
-    __align__(16) __nv_bfloat16 xs[64 * kW1S];
-    __align__(16) __nv_bfloat16 h1s[64 * kW2S];
-    __align__(16) __nv_bfloat16 d1s[64 * kW2S];
-    __align__(16) __nv_bfloat16 d2s[64 * kW2S];
-    // per-warp partial sums (each written by one warp only, summed in warp order at the end), so the
-    // block's result does not depend on the order in which its warps run
-    __align__(16) float db1[kMT / 32][kHid];
-    float db2[kMT / 32][kHid], dw3[kMT / 32][kHid];
+// ---- 5. training on the 5th-generation tensor cores (tcgen05) -------------------
+// One CTA walks tiles of 128 feature rows, one row per thread (= TMEM lane).
+// Per tile, four groups of tcgen05.mma (M = 128, FP32 accumulators in TMEM,
+// BF16 operands in shared memory in the canonical K-major layout, issued by
+// one thread and committed to an mbarrier):
+//   layer 1   D = X W1^T               (N = 64, K = 32)  -> h1 = bf16(tanh(D + b1))
+//   layer 2   D = H1 W2^T              (N = 64, K = 64)  -> h2 = tanh(D + b2), y
+//   backward  D = dZ2 W2               (N = 64, K = 64)  -> dZ1 = D (1 - h1^2)
+//   gradients G += [dZ2^T; dZ1^T] [H1 | X | 1]           (M = 128, N = 112, K = the tile's 128 rows)
+// so that rows 0-63 of G hold dW2 (columns 0-63) and db2 (column 96), and rows
+// 64-127 hold dW1 (columns 64-80) and db1 (column 96); G accumulates over the
+// CTA's tiles.  dz3 = d(squared error)/dz3 = 2 (y - t) y (1 - y) per row; dw3,
+// db3 and the loss are summed over the warp's rows by shuffles into per-warp
+// partials (added in warp order at the end), so a CTA's result does not
+// depend on the order in which its warps run.  The forward-only variant
+// (BWD = false) writes y and stops after layer 2.
+constexpr uint32_t kIdescM128N112 =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((112u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kTrainTmemCols = 256;  // D in columns 0-63, G in 128-239
+constexpr int kGN = 112;                  // rows of the gradient B operand
+constexpr int kPartStride = LCP_MLP_NPARAMS + 4;  // a CTA's partial: the parameters, then the loss (16-byte rows)
+
+struct TrainSmem {
+    __align__(1024) __nv_bfloat16 W1[kHid * kFS];    // B of layer 1: N = 64 units x K = 32 features
+    __align__(1024) __nv_bfloat16 W2[kHid * kHid];   // B of layer 2: N = 64 outputs x K = 64 inputs
+    __align__(1024) __nv_bfloat16 W2t[kHid * kHid];  // B of the backward product: N = 64 inputs x K = 64 outputs
+    __align__(1024) __nv_bfloat16 X[128 * kFS];      // A of layer 1: the tile's feature rows
+    __align__(1024) __nv_bfloat16 H1[128 * kHid];    // A of layer 2: h1 rows
+    __align__(1024) __nv_bfloat16 DZ2[128 * kHid];   // A of the backward product: dZ2 rows
+    __align__(1024) __nv_bfloat16 Ag[128 * 128];     // A of the gradients: dZ2^T (rows 0-63), dZ1^T (64-127)
+    __align__(1024) __nv_bfloat16 Bg[kGN * 128];     // B: H1^T (rows 0-63), X^T (64-95), ones (96), zeros
+    float b1[kHid], b2[kHid], w3[kHid];
+    float dw3[kMT / 32][kHid];
     float db3[kMT / 32], loss[kMT / 32];
+    __align__(8) uint64_t mbar;
+    uint32_t tmem;
+    int abort_flag;  // set when an mbarrier wait gave up; read by all threads after a barrier
 };
+constexpr size_t kTrainSmemBytes = sizeof(TrainSmem) + 1024;
 
-static_assert(offsetof(BwdSmem, xs) % 16 == 0 && offsetof(BwdSmem, h1s) % 16 == 0 &&
-                  offsetof(BwdSmem, d1s) % 16 == 0 && offsetof(BwdSmem, d2s) % 16 == 0,
-              "ldmatrix rows must be 16-byte aligned");
-static_assert((kW1S * 2) % 16 == 0 && (kW2S * 2) % 16 == 0, "row strides must keep 16-byte alignment");
-
-__device__ __forceinline__ void st_pair(__nv_bfloat16* base, int row, int col, int stride, uint32_t w) {
-    *reinterpret_cast<uint32_t*>(base + row * stride + col) = w;
+__device__ __forceinline__ void put_canon(__nv_bfloat16* tile, int row, int k, int kg, __nv_bfloat16 v) {
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(tile) + canon_off(row, k, kg)) = v;
 }
-
-// Column sums over the 8 row groups of a warp (lanes with equal tig).
-__device__ __forceinline__ float sum_over_gid(float x) {
-    x += __shfl_xor_sync(0xFFFFFFFFu, x, 4);
-    x += __shfl_xor_sync(0xFFFFFFFFu, x, 8);
-    x += __shfl_xor_sync(0xFFFFFFFFu, x, 16);
-    return x;
+__device__ __forceinline__ void put_canon16(__nv_bfloat16* tile, int row, int k, int kg, uint4 v) {  // k % 8 == 0
+    *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(tile) + canon_off(row, k, kg)) = v;
 }
-
-// One CTA's gradient sums go either straight into grad (atomic adds, scaled by
-// 1/n) or, for the deterministic variant, unscaled into its own row `part` of
-// [gridDim.x][kPartStride] floats (every entry written), which
-// bwd_reduce_kernel then sums over the CTAs in CTA order.
-constexpr int kPartStride = LCP_MLP_NPARAMS + 4;  // the parameters, then the loss (16-byte rows)
-
-template <bool DET>
-__global__ void __launch_bounds__(kMT) mlp_backward_kernel(const float* __restrict__ prm,
-                                                          const __nv_bfloat16* __restrict__ feat,
-                                                          const float* __restrict__ prior,
-                                                          const float* __restrict__ target, int64_t n,
-                                                          float* __restrict__ grad, float* __restrict__ loss,
-                                                          float* __restrict__ parts) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
-    load_net(prm, S.net, S.W2t);
-    for (int q = threadIdx.x; q < (kMT / 32) * kHid; q += blockDim.x) {
-        (&S.db1[0][0])[q] = 0.f;
-        (&S.db2[0][0])[q] = 0.f;
-        (&S.dw3[0][0])[q] = 0.f;
-    }
-    if (threadIdx.x < kMT / 32) S.db3[threadIdx.x] = S.loss[threadIdx.x] = 0.f;
+__device__ __forceinline__ uint4 get_canon16(const __nv_bfloat16* tile, int row, int k, int kg) {
+    return *reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(tile) + canon_off(row, k, kg));
+}
+__device__ __forceinline__ __nv_bfloat16 bf16_bits(uint32_t w, int hi) {
+    const unsigned short s = (unsigned short)(hi ? (w >> 16) : (w & 0xFFFFu));
+    return *reinterpret_cast<const __nv_bfloat16*>(&s);
+}
+// Generic-proxy shared-memory writes visible to the tensor core, every thread's
+// earlier TMEM reads ordered before the MMAs issued next, all threads past.
+__device__ __forceinline__ void tc_handoff() {
+    fence_async_smem();
+    tc_fence_before();
     __syncthreads();
-    const NetSmem& s = S.net;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
-    const float inv_n = 1.0f / (float)n;
-    float gW2[8][4], gW1[4][4];
-#pragma unroll
-    for (int a = 0; a < 8; ++a) gW2[a][0] = gW2[a][1] = gW2[a][2] = gW2[a][3] = 0.f;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) gW1[a][0] = gW1[a][1] = gW1[a][2] = gW1[a][3] = 0.f;
-    const int rw = 16 * warp;  // this warp's rows inside the staged 64
+    tc_fence_after();
+}
 
-    for (int64_t base = (int64_t)blockIdx.x * 64; base < n; base += (int64_t)gridDim.x * 64) {
-        const int64_t r0 = base + rw;
-        {  // stage X
-            const int r = lane >> 1, h = lane & 1;
-            uint4 a = make_uint4(0, 0, 0, 0), b = a;
-            if (r0 + r < n) {
-                const uint4* src = reinterpret_cast<const uint4*>(feat + (r0 + r) * kFS) + 2 * h;
-                a = __ldg(src);
-                b = __ldg(src + 1);
-            }
-            uint4* dst = reinterpret_cast<uint4*>(S.xs + (rw + r) * kW1S + 16 * h);
-            dst[0] = a;
-            dst[1] = b;
+template <bool BWD, bool DET>
+__global__ void __launch_bounds__(kMT, 1) mlp_train_tc_kernel(const float* __restrict__ prm,
+                                                              const __nv_bfloat16* __restrict__ feat,
+                                                              const float* __restrict__ prior,
+                                                              const float* __restrict__ target, int64_t n,
+                                                              float* __restrict__ y, float* __restrict__ grad,
+                                                              float* __restrict__ loss, float* __restrict__ parts) {
+    extern __shared__ __align__(1024) unsigned char tr_raw[];
+    TrainSmem& S = *reinterpret_cast<TrainSmem*>(tr_raw + ((1024 - (smem_addr(tr_raw) & 1023)) & 1023));
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int kg1 = kFS / 8, kg2 = kHid / 8, kgG = 128 / 8;  // core matrices along K
+    // weights into the canonical layouts (bf16), vectors as fp32
+    for (int q = t; q < kHid * kFS; q += kMT) {
+        const int u = q / kFS, f = q - u * kFS;
+        put_canon(S.W1, u, f, kg1, __float2bfloat16_rn(f < 17 ? prm[kOffW1 + q] : 0.f));
+    }
+    for (int q = t; q < kHid * kHid; q += kMT) {
+        const int o = q >> 6, i = q & 63;
+        const __nv_bfloat16 w = __float2bfloat16_rn(prm[kOffW2 + q]);
+        put_canon(S.W2, o, i, kg2, w);
+        if (BWD) put_canon(S.W2t, i, o, kg2, w);
+    }
+    for (int q = t; q < kHid; q += kMT) {
+        S.b1[q] = prm[kOffB1 + q];
+        S.b2[q] = prm[kOffB2 + q];
+        S.w3[q] = prm[kOffW3 + q];
+    }
+    if (BWD) {
+        // the rows of Bg that no tile rewrites: X^T of the zero features 17-31, the ones, the zeros
+        for (int q = t; q < (kGN - 81) * 128; q += kMT) {
+            const int rr = 81 + q / 128, k = q % 128;
+            put_canon(S.Bg, rr, k, kgG, __float2bfloat16_rn(rr == 96 ? 1.f : 0.f));
         }
-        __syncwarp();
-        uint32_t x[2][4], h1[4][4];
-        float h2[8][4];
-        load_x_frags(S.xs + rw * kW1S, x, lane);
-        forward16(s, x, h1, h2, gid, tig);
-        const float2 z = output16(s, h2, tig);
-        const bool vlo = r0 + gid < n, vhi = r0 + gid + 8 < n;
-        const float plo = (prior && vlo) ? __ldg(prior + r0 + gid) : 0.f;
-        const float phi = (prior && vhi) ? __ldg(prior + r0 + gid + 8) : 0.f;
-        const float ylo = sigmoid(z.x + plo), yhi = sigmoid(z.y + phi);
-        const float tlo = vlo ? __ldg(target + r0 + gid) : 0.f, thi = vhi ? __ldg(target + r0 + gid + 8) : 0.f;
+        for (int q = t; q < (kMT / 32) * kHid; q += kMT) (&S.dw3[0][0])[q] = 0.f;
+        if (t < kMT / 32) S.db3[t] = S.loss[t] = 0.f;
+    }
+    if (t == 0) {
+        S.abort_flag = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&S.tmem)),
+                     "r"(kTrainTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_handoff();  // weights, constant rows, TMEM address and mbarrier are ready
+    const uint32_t tmem = S.tmem, tmem_g = tmem + 128;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16), lane_g = lane_base + 128;
+    const uint32_t mbar = smem_addr(&S.mbar);
+    const uint32_t aX = smem_addr(S.X), aH = smem_addr(S.H1), aD = smem_addr(S.DZ2), aG = smem_addr(S.Ag);
+    const uint32_t bW1 = smem_addr(S.W1), bW2 = smem_addr(S.W2), bW2t = smem_addr(S.W2t), bG = smem_addr(S.Bg);
+    const float b3 = prm[kOffB3];
+    uint32_t phase = 0;
+    volatile int* abort_flag = &S.abort_flag;
+    bool any = false;  // G holds this CTA's sums (uniform)
+    auto mma_wait = [&]() {
+        if (!mbar_wait(mbar, phase)) *abort_flag = 1;
+        phase ^= 1u;
+        tc_fence_after();
+    };
+    const int64_t ntiles = (n + 127) / 128;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r = tile * 128 + t;
+        const bool valid = r < n;
+        // features: X (A of layer 1) and X^T (rows 64-80 of Bg); rows beyond n are zero
+        uint4 xr[kFS / 8];
+#pragma unroll
+        for (int g = 0; g < kFS / 8; ++g) {
+            xr[g] = valid ? __ldg(reinterpret_cast<const uint4*>(feat + r * kFS) + g) : make_uint4(0, 0, 0, 0);
+            put_canon16(S.X, t, 8 * g, kg1, xr[g]);
+        }
+        if (BWD) {
+            const uint32_t* xw = reinterpret_cast<const uint32_t*>(xr);
+#pragma unroll
+            for (int f = 0; f < 17; ++f) put_canon(S.Bg, 64 + f, t, kgG, bf16_bits(xw[f >> 1], f & 1));
+        }
+        tc_handoff();
+        if (*abort_flag) break;  // uniform: read after the barrier, written only before one
+        if (t == 0) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+                tc_mma(tmem, smem_desc(aX + 256 * s, 128, 128 * kg1), smem_desc(bW1 + 256 * s, 128, 128 * kg1), s);
+            tc_commit(mbar);
+        }
+        mma_wait();
+        // h1 = bf16(tanh(D + b1)): H1 (A of layer 2) and H1^T (rows 0-63 of Bg)
+#pragma unroll
+        for (int cg = 0; cg < 4; ++cg) {
+            float z[16];
+            tmem_ld16(lane_base + 16 * cg, z);
+            uint32_t hw[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                hw[e] = pack_bf16(tanh_fast(z[2 * e] + S.b1[16 * cg + 2 * e]),
+                                  tanh_fast(z[2 * e + 1] + S.b1[16 * cg + 2 * e + 1]));
+            put_canon16(S.H1, t, 16 * cg, kg2, make_uint4(hw[0], hw[1], hw[2], hw[3]));
+            put_canon16(S.H1, t, 16 * cg + 8, kg2, make_uint4(hw[4], hw[5], hw[6], hw[7]));
+            if (BWD) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) put_canon(S.Bg, 16 * cg + e, t, kgG, bf16_bits(hw[e >> 1], e & 1));
+            }
+        }
+        tc_handoff();
+        if (*abort_flag) break;
+        if (t == 0) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                tc_mma(tmem, smem_desc(aH + 256 * s, 128, 128 * kg2), smem_desc(bW2 + 256 * s, 128, 128 * kg2), s);
+            tc_commit(mbar);
+        }
+        mma_wait();
+        // output: y = sigmoid(b3 + prior + w3 . tanh(D + b2))
+        float z3 = b3 + ((prior && valid) ? __ldg(prior + r) : 0.f);
+#pragma unroll
+        for (int cg = 0; cg < 4; ++cg) {
+            float z[16];
+            tmem_ld16(lane_base + 16 * cg, z);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) z3 = fmaf(tanh_fast(z[e] + S.b2[16 * cg + e]), S.w3[16 * cg + e], z3);
+        }
+        const float yv = sigmoid(z3);
+        if (!BWD) {
+            if (valid) y[r] = yv;
+            tc_fence_before();  // this tile's TMEM reads are ordered before the next MMA
+            continue;
+        }
+        const float tv = valid ? __ldg(target + r) : 0.f;
         // d(sum of squared errors)/dz3 = 2 (y - t) y (1 - y); the 1/n of the mean is applied once at the end
-        const float dlo = vlo ? 2.f * (ylo - tlo) * ylo * (1.f - ylo) : 0.f;
-        const float dhi = vhi ? 2.f * (yhi - thi) * yhi * (1.f - yhi) : 0.f;
-        {  // the warp's sums over its 16 rows (each row once: the lanes with tig == 0), fixed order
-            const float e = tig == 0 ? (vlo ? (ylo - tlo) * (ylo - tlo) : 0.f) + (vhi ? (yhi - thi) * (yhi - thi) : 0.f)
-                                     : 0.f;
-            const float dd = tig == 0 ? dlo + dhi : 0.f;
-            const float es = sum_over_gid(e), ds = sum_over_gid(dd);
-            if (lane == 0) {
-                S.loss[warp] += es;
-                S.db3[warp] += ds;
+        const float dz3 = valid ? 2.f * (yv - tv) * yv * (1.f - yv) : 0.f;
+        const float err2 = valid ? (yv - tv) * (yv - tv) : 0.f;
+        // dZ2 = dz3 w3 (1 - h2^2): DZ2 (A of the backward product) and dZ2^T (rows 0-63 of Ag);
+        // dw3 = sum over rows of dz3 h2, reduced over the warp 16 columns at a time
+#pragma unroll
+        for (int cg = 0; cg < 4; ++cg) {
+            float z[16], ev[16];
+            tmem_ld16(lane_base + 16 * cg, z);
+            uint32_t dw[8];
+#pragma unroll
+            for (int e = 0; e < 16; e += 2) {
+                const float h0 = tanh_fast(z[e] + S.b2[16 * cg + e]), h1v = tanh_fast(z[e + 1] + S.b2[16 * cg + e + 1]);
+                ev[e] = dz3 * h0;
+                ev[e + 1] = dz3 * h1v;
+                dw[e >> 1] = pack_bf16(dz3 * S.w3[16 * cg + e] * (1.f - h0 * h0),
+                                       dz3 * S.w3[16 * cg + e + 1] * (1.f - h1v * h1v));
             }
-        }
-        // stage h1 (its A fragments are C fragments of 8-column tiles 2ks, 2ks+1)
+            put_canon16(S.DZ2, t, 16 * cg, kg2, make_uint4(dw[0], dw[1], dw[2], dw[3]));
+            put_canon16(S.DZ2, t, 16 * cg + 8, kg2, make_uint4(dw[4], dw[5], dw[6], dw[7]));
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-            st_pair(S.h1s, rw + gid, 16 * ks + 2 * tig, kW2S, h1[ks][0]);
-            st_pair(S.h1s, rw + gid + 8, 16 * ks + 2 * tig, kW2S, h1[ks][1]);
-            st_pair(S.h1s, rw + gid, 16 * ks + 8 + 2 * tig, kW2S, h1[ks][2]);
-            st_pair(S.h1s, rw + gid + 8, 16 * ks + 8 + 2 * tig, kW2S, h1[ks][3]);
-        }
-        // dZ2 = dz3 w3 (1 - h2^2); dw3 += h2^T dz3; db2 += column sums of dZ2
-        uint32_t d2[4][4];
+            for (int e = 0; e < 16; ++e) put_canon(S.Ag, 16 * cg + e, t, kgG, bf16_bits(dw[e >> 1], e & 1));
+            // reduce-scatter of the 16 columns over the 32 lanes: lanes 2c and 2c + 1 end with column c
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            float dz[4];
+            for (int w = 16, m = 8; m >= 1; w >>= 1, m >>= 1) {
+                const bool up = (lane & w) != 0;
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int col = 8 * nt + 2 * tig + e;
-                const float w = s.w3[col];
-                dz[e] = dlo * w * (1.f - h2[nt][e] * h2[nt][e]);
-                dz[2 + e] = dhi * w * (1.f - h2[nt][2 + e] * h2[nt][2 + e]);
-                const float gw3 = sum_over_gid(h2[nt][e] * dlo + h2[nt][2 + e] * dhi);
-                const float gb2 = sum_over_gid(dz[e] + dz[2 + e]);
-                if (gid == 0) {  // one lane per column of this warp
-                    S.dw3[warp][col] += gw3;
-                    S.db2[warp][col] += gb2;
+                for (int e = 0; e < m; ++e) {
+                    const float give = up ? ev[e] : ev[m + e];
+                    const float keep = up ? ev[m + e] : ev[e];
+                    ev[e] = keep + __shfl_xor_sync(0xFFFFFFFFu, give, w);
                 }
             }
-            const uint32_t lo = pack_bf16(dz[0], dz[1]), hi = pack_bf16(dz[2], dz[3]);
-            d2[nt >> 1][(nt & 1) * 2 + 0] = lo;
-            d2[nt >> 1][(nt & 1) * 2 + 1] = hi;
-            st_pair(S.d2s, rw + gid, 8 * nt + 2 * tig, kW2S, lo);
-            st_pair(S.d2s, rw + gid + 8, 8 * nt + 2 * tig, kW2S, hi);
+            ev[0] += __shfl_xor_sync(0xFFFFFFFFu, ev[0], 1);
+            if ((lane & 1) == 0) S.dw3[warp][16 * cg + (lane >> 1)] += ev[0];
         }
-        // dA1 = dZ2 W2^T; B(k = output unit, n = input unit) = W2t[n][k]
-        float da[8][4];
+        {  // db3 and the loss: the warp's rows, fixed order
+            float a = dz3, l = err2;
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) da[nt][0] = da[nt][1] = da[nt][2] = da[nt][3] = 0.f;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks)
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const __nv_bfloat16* w = S.W2t + (8 * nt + gid) * kW2S + 16 * ks + 2 * tig;
-                mma16816(da[nt], d2[ks], *reinterpret_cast<const uint32_t*>(w),
-                         *reinterpret_cast<const uint32_t*>(w + 8));
+            for (int w = 16; w >= 1; w >>= 1) {
+                a += __shfl_xor_sync(0xFFFFFFFFu, a, w);
+                l += __shfl_xor_sync(0xFFFFFFFFu, l, w);
             }
-        // dZ1 = dA1 (1 - h1^2); db1 += column sums
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const float2 hl = unpack_bf16(h1[nt >> 1][(nt & 1) * 2 + 0]);
-            const float2 hh = unpack_bf16(h1[nt >> 1][(nt & 1) * 2 + 1]);
-            const float z0 = da[nt][0] * (1.f - hl.x * hl.x), z1 = da[nt][1] * (1.f - hl.y * hl.y);
-            const float z2 = da[nt][2] * (1.f - hh.x * hh.x), z3 = da[nt][3] * (1.f - hh.y * hh.y);
-            st_pair(S.d1s, rw + gid, 8 * nt + 2 * tig, kW2S, pack_bf16(z0, z1));
-            st_pair(S.d1s, rw + gid + 8, 8 * nt + 2 * tig, kW2S, pack_bf16(z2, z3));
-            const float g0 = sum_over_gid(z0 + z2), g1 = sum_over_gid(z1 + z3);
-            if (gid == 0) {
-                S.db1[warp][8 * nt + 2 * tig] += g0;
-                S.db1[warp][8 * nt + 2 * tig + 1] += g1;
+            if (lane == 0) {
+                S.db3[warp] += a;
+                S.loss[warp] += l;
             }
         }
-        __syncthreads();
-        // weight gradients over the 64 staged rows: this warp's 16 output rows
-        const int o0 = 16 * warp;
-        const int ar = (lane & 7) + ((lane >> 4) & 1) * 8, ac = ((lane >> 3) & 1) * 8;  // A^T operand addressing
-        const int br = (lane & 7) + ((lane >> 3) & 1) * 8, bc = (lane >> 4) * 8;        // B operand addressing
+        tc_handoff();
+        if (*abort_flag) break;
+        if (t == 0) {  // dA1 = dZ2 W2
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            uint32_t a2[4], a1[4];
-            ldsm_x4_t(a2, S.d2s + (16 * kk + ar) * kW2S + o0 + ac);
-            ldsm_x4_t(a1, S.d1s + (16 * kk + ar) * kW2S + o0 + ac);
+            for (int s = 0; s < 4; ++s)
+                tc_mma(tmem, smem_desc(aD + 256 * s, 128, 128 * kg2), smem_desc(bW2t + 256 * s, 128, 128 * kg2), s);
+            tc_commit(mbar);
+        }
+        mma_wait();
+        // dZ1 = dA1 (1 - h1^2), h1 as rounded for layer 2: dZ1^T (rows 64-127 of Ag)
 #pragma unroll
-            for (int np = 0; np < 4; ++np) {  // dW2: input units in pairs of 8-column tiles
-                uint32_t b[4];
-                ldsm_x4_t(b, S.h1s + (16 * kk + br) * kW2S + 16 * np + bc);
-                mma16816(gW2[2 * np], a2, b[0], b[1]);
-                mma16816(gW2[2 * np + 1], a2, b[2], b[3]);
-            }
+        for (int cg = 0; cg < 4; ++cg) {
+            float z[16];
+            tmem_ld16(lane_base + 16 * cg, z);
+            const uint4 ha = get_canon16(S.H1, t, 16 * cg, kg2), hb = get_canon16(S.H1, t, 16 * cg + 8, kg2);
+            const uint32_t hw[8] = {ha.x, ha.y, ha.z, ha.w, hb.x, hb.y, hb.z, hb.w};
 #pragma unroll
-            for (int np = 0; np < 2; ++np) {  // dW1: features 0-15, 16-31
-                uint32_t b[4];
-                ldsm_x4_t(b, S.xs + (16 * kk + br) * kW1S + 16 * np + bc);
-                mma16816(gW1[2 * np], a1, b[0], b[1]);
-                mma16816(gW1[2 * np + 1], a1, b[2], b[3]);
+            for (int e = 0; e < 16; e += 2) {
+                const float2 h = unpack_bf16(hw[e >> 1]);
+                const uint32_t d1 = pack_bf16(z[e] * (1.f - h.x * h.x), z[e + 1] * (1.f - h.y * h.y));
+                put_canon(S.Ag, 64 + 16 * cg + e, t, kgG, bf16_bits(d1, 0));
+                put_canon(S.Ag, 64 + 16 * cg + e + 1, t, kgG, bf16_bits(d1, 1));
             }
         }
-        __syncthreads();
+        tc_handoff();
+        if (*abort_flag) break;
+        if (t == 0) {  // G += [dZ2^T; dZ1^T] [H1 | X | 1] over the tile's 128 rows
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                tc_mma(tmem_g, smem_desc(aG + 256 * s, 128, 128 * kgG), smem_desc(bG + 256 * s, 128, 128 * kgG),
+                       (any || s > 0) ? 1u : 0u, kIdescM128N112);
+            tc_commit(mbar);
+        }
+        mma_wait();  // the MMAs have read this tile's operands before the next tile rewrites them
+        any = true;
     }
-    // this CTA's sums: the weight matrices from this warp's registers (its own 16 output rows), the
-    // vectors from the per-warp partials in warp order
-    float* const row = DET ? parts + (int64_t)blockIdx.x * kPartStride : nullptr;
-    auto put = [&](int idx, float val) {
-        if (DET) row[idx] = val;
-        else atomicAdd(grad + idx, val * inv_n);
-    };
-    const int o0 = 16 * warp;
+    if (BWD) {
+        // this CTA's sums: thread t holds row t of G (TMEM lane t)
+        const float inv_n = 1.0f / (float)n;
+        float* const row = DET ? parts + (int64_t)blockIdx.x * kPartStride : nullptr;
+        auto put = [&](int idx, float val) {
+            if (DET) row[idx] = val;
+            else atomicAdd(grad + idx, val * inv_n);
+        };
+        float gsum[kGN];
+        if (any) {
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
+            for (int cg = 0; cg < kGN / 16; ++cg) {
+                float z[16];
+                tmem_ld16(lane_g + 16 * cg, z);
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int col = 8 * nt + 2 * tig + e;
-            put(kOffW2 + (o0 + gid) * kHid + col, gW2[nt][e]);
-            put(kOffW2 + (o0 + gid + 8) * kHid + col, gW2[nt][2 + e]);
+                for (int e = 0; e < 16; ++e) gsum[16 * cg + e] = z[e];
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < kGN; ++e) gsum[e] = 0.f;
         }
+        if (t < kHid) {  // dW2 row t, db2[t]
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
+            for (int i = 0; i < kHid; ++i) put(kOffW2 + t * kHid + i, gsum[i]);
+            put(kOffB2 + t, gsum[96]);
+        } else {  // dW1 row u, db1[u]
+            const int u = t - kHid;
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int col = 8 * nt + 2 * tig + e;
-            if (col < 17) {
-                put(kOffW1 + (o0 + gid) * kFS + col, gW1[nt][e]);
-                put(kOffW1 + (o0 + gid + 8) * kFS + col, gW1[nt][2 + e]);
-            } else if (DET) {  // the zero columns of W1: every entry of the row is written
-                row[kOffW1 + (o0 + gid) * kFS + col] = 0.f;
-                row[kOffW1 + (o0 + gid + 8) * kFS + col] = 0.f;
+            for (int f = 0; f < kFS; ++f) {
+                if (f < 17) put(kOffW1 + u * kFS + f, gsum[64 + f]);
+                else if (DET) row[kOffW1 + u * kFS + f] = 0.f;  // the zero columns of W1: every entry written
+            }
+            put(kOffB1 + u, gsum[96]);
+        }
+        __syncthreads();
+        for (int q = t; q < kHid; q += kMT) {
+            float c = 0.f;
+#pragma unroll
+            for (int w = 0; w < kMT / 32; ++w) c += S.dw3[w][q];
+            put(kOffW3 + q, c);
+        }
+        if (t == 0) {
+            float a = 0.f, l = 0.f;
+#pragma unroll
+            for (int w = 0; w < kMT / 32; ++w) {
+                a += S.db3[w];
+                l += S.loss[w];
+            }
+            put(kOffB3, a);
+            if (DET) {
+                for (int q = kOffB3 + 1; q < LCP_MLP_NPARAMS; ++q) row[q] = 0.f;  // padding
+                row[LCP_MLP_NPARAMS] = l;
+            } else if (loss) {
+                atomicAdd(loss, l * inv_n);
             }
         }
+    }
+    tc_fence_before();
     __syncthreads();
-    for (int q = threadIdx.x; q < kHid; q += blockDim.x) {
-        float a = 0.f, b = 0.f, c = 0.f;
-#pragma unroll
-        for (int w = 0; w < kMT / 32; ++w) {
-            a += S.db1[w][q];
-            b += S.db2[w][q];
-            c += S.dw3[w][q];
-        }
-        put(kOffB1 + q, a);
-        put(kOffB2 + q, b);
-        put(kOffW3 + q, c);
-    }
-    if (threadIdx.x == 0) {
-        float a = 0.f, l = 0.f;
-#pragma unroll
-        for (int w = 0; w < kMT / 32; ++w) {
-            a += S.db3[w];
-            l += S.loss[w];
-        }
-        put(kOffB3, a);
-        if (DET) {
-            for (int q = kOffB3 + 1; q < LCP_MLP_NPARAMS; ++q) row[q] = 0.f;  // padding
-            row[LCP_MLP_NPARAMS] = l;
-        } else if (loss) {
-            atomicAdd(loss, l * inv_n);
-        }
-    }
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTrainTmemCols) : "memory");
 }
 
 // grad[q] = (sum over CTAs, in CTA order, of their partial q) / n; the loss likewise.
@@ -965,7 +831,7 @@ __global__ void bwd_reduce_kernel(const float* __restrict__ parts, int nparts, f
     }
 }
 
-// ---- 7. Adam ---------------------------------------------------------------------
+// ---- 6. Adam ---------------------------------------------------------------------
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
                             float c2) {
@@ -1048,18 +914,9 @@ extern "C" lcp_status lcp_surrogate_features(const float* mom, int H, int W, dou
     return check_launch("lcp_surrogate_features");
 }
 
-extern "C" lcp_status lcp_mlp_forward(const float* params, const void* feat, const float* prior, int64_t n, float* y,
-                                      lcp_stream_t stream) {
-    if (!params || !feat || !y || n < 1 || !aligned16(feat))
-        return fail(LCP_ERR_ARG, "lcp_mlp_forward: NULL/misaligned pointer or n < 1");
-    mlp_forward_kernel<<<grid_for(n, 64, 8), kMT, 0, (cudaStream_t)stream>>>(
-        params, (const __nv_bfloat16*)feat, prior, n, y);
-    return check_launch("lcp_mlp_forward");
-}
-
 namespace {
-// Shared-memory size of both backward variants, set once per device.
-lcp_status prepare_backward(const char* fn) {
+// The training kernels' shared memory (about 124 KB: one CTA per SM), set once per device.
+lcp_status prepare_train(const char* fn) {
     static std::mutex mu;
     static bool set[64] = {false};
     int dev = 0;
@@ -1069,17 +926,23 @@ lcp_status prepare_backward(const char* fn) {
     }
     std::lock_guard<std::mutex> lk(mu);
     if (!set[dev]) {
-        if (cudaFuncSetAttribute(mlp_backward_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(BwdSmem)) != cudaSuccess ||
-            cudaFuncSetAttribute(mlp_backward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(BwdSmem)) != cudaSuccess) {
+        const int b = (int)kTrainSmemBytes;
+        if (cudaFuncSetAttribute(mlp_train_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(mlp_train_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(mlp_train_tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) !=
+                cudaSuccess) {
             cudaGetLastError();
-            return fail(LCP_ERR_CUDA, "%s: %zu bytes of shared memory not available", fn, sizeof(BwdSmem));
+            return fail(LCP_ERR_CUDA, "%s: %zu bytes of shared memory not available", fn, kTrainSmemBytes);
         }
         set[dev] = true;
     }
     return LCP_OK;
 }
+
+// 128-row tiles, one CTA per SM walking them.
+int train_grid(int64_t n) { return grid_for(n, 128, 1); }
 
 lcp_status check_backward(const char* fn, const float* params, const void* feat, const float* target, float* grad,
                           int64_t n) {
@@ -1089,25 +952,37 @@ lcp_status check_backward(const char* fn, const float* params, const void* feat,
 }
 }  // namespace
 
+extern "C" lcp_status lcp_mlp_forward(const float* params, const void* feat, const float* prior, int64_t n, float* y,
+                                      lcp_stream_t stream) {
+    static const char* fn = "lcp_mlp_forward";
+    if (!params || !feat || !y || n < 1 || !aligned16(feat))
+        return fail(LCP_ERR_ARG, "%s: NULL/misaligned pointer or n < 1", fn);
+    lcp_status s = prepare_train(fn);
+    if (s != LCP_OK) return s;
+    mlp_train_tc_kernel<false, false><<<train_grid(n), kMT, kTrainSmemBytes, (cudaStream_t)stream>>>(
+        params, (const __nv_bfloat16*)feat, prior, nullptr, n, y, nullptr, nullptr, nullptr);
+    return check_launch(fn);
+}
+
 extern "C" lcp_status lcp_mlp_backward(const float* params, const void* feat, const float* prior, const float* target,
                                        int64_t n, float* grad, float* loss, lcp_stream_t stream) {
     static const char* fn = "lcp_mlp_backward";
     lcp_status s = check_backward(fn, params, feat, target, grad, n);
-    if (s != LCP_OK || (s = prepare_backward(fn)) != LCP_OK) return s;
+    if (s != LCP_OK || (s = prepare_train(fn)) != LCP_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(grad, 0, LCP_MLP_NPARAMS * sizeof(float), st) != cudaSuccess ||
         (loss && cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess)) {
         cudaGetLastError();
         return fail(LCP_ERR_CUDA, "%s: clearing the outputs failed", fn);
     }
-    mlp_backward_kernel<false><<<grid_for(n, 64, 2), kMT, sizeof(BwdSmem), st>>>(
-        params, (const __nv_bfloat16*)feat, prior, target, n, grad, loss, nullptr);
+    mlp_train_tc_kernel<true, false><<<train_grid(n), kMT, kTrainSmemBytes, st>>>(
+        params, (const __nv_bfloat16*)feat, prior, target, n, nullptr, grad, loss, nullptr);
     return check_launch(fn);
 }
 
 extern "C" size_t lcp_mlp_backward_workspace_bytes(int64_t n) {
     if (n < 1) return 0;
-    return (size_t)grid_for(n, 64, 2) * kPartStride * sizeof(float);
+    return (size_t)train_grid(n) * kPartStride * sizeof(float);
 }
 
 extern "C" lcp_status lcp_mlp_backward_ws(const float* params, const void* feat, const float* prior,
@@ -1116,15 +991,15 @@ extern "C" lcp_status lcp_mlp_backward_ws(const float* params, const void* feat,
     static const char* fn = "lcp_mlp_backward_ws";
     lcp_status s = check_backward(fn, params, feat, target, grad, n);
     if (s != LCP_OK) return s;
-    const int grid = grid_for(n, 64, 2);
+    const int grid = train_grid(n);
     const size_t need = (size_t)grid * kPartStride * sizeof(float);
     if (!workspace || !aligned16(workspace) || workspace_bytes < need)
         return fail(LCP_ERR_ARG, "%s: need a 16-byte aligned workspace of %zu bytes", fn, need);
-    if ((s = prepare_backward(fn)) != LCP_OK) return s;
+    if ((s = prepare_train(fn)) != LCP_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     float* parts = reinterpret_cast<float*>(workspace);
-    mlp_backward_kernel<true><<<grid, kMT, sizeof(BwdSmem), st>>>(params, (const __nv_bfloat16*)feat, prior, target,
-                                                                    n, grad, loss, parts);
+    mlp_train_tc_kernel<true, true><<<grid, kMT, kTrainSmemBytes, st>>>(params, (const __nv_bfloat16*)feat, prior,
+                                                                       target, n, nullptr, grad, loss, parts);
     if ((s = check_launch(fn)) != LCP_OK) return s;
     bwd_reduce_kernel<<<(LCP_MLP_NPARAMS + 1 + 255) / 256, 256, 0, st>>>(parts, grid, 1.0f / (float)n, grad, loss);
     return check_launch(fn);

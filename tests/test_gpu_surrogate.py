@@ -233,7 +233,7 @@ def test_infer_equals_forward_over_features_and_oracle(lib, h, w):
     out = G.lcp_mlp_infer(mom, iso, prm)
     feat, prior = G.lcp_surrogate_features(mom, iso)
     via = G.lcp_mlp_forward(prm, feat, prior).reshape(len(iso), h - 1, w - 1)
-    # the fused kernel (tcgen05, layer-1 tanh in bf16) and the row kernel (mma.sync) on the same feature
+    # the fused kernel (layer-1 tanh in bf16) and the row kernel (layer-1 tanh in fp32), both tcgen05, on the same feature
     # rows: both round h1 to bf16; they differ by an ulp of h1 here and there and the summation order
     assert torch.allclose(out, via, atol=5e-3, rtol=0), float((out - via).abs().max())
     fref = _features_ref(d["u"], d["v"], iso).reshape(-1, 17)
