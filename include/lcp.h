@@ -211,6 +211,31 @@ lcp_status lcp_fused_static_ws(const void* u, const void* v, lcp_dtype in_dtype,
                                void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, lcp_stream_t stream);
 
 /*
+ * lcp_fused_host - the closed-form LCP map of lcp_fused_ws (statistics of
+ * Sec. 3.1, the divergence Gaussian of Eqs. 2/3, the LCP of every cell of the
+ * last paragraph of Sec. 3.1, and the mean-field mask) for callers whose
+ * ensembles and results live in host memory, end to end in one call.
+ * u, v: device memory, or pinned host memory the device can address
+ * (cudaHostAlloc, cudaHostRegister), read in place, each member byte once over
+ * the CPU-GPU link; pageable memory is rejected with LCP_ERR_ARG (copy it into
+ * pinned or device memory first).  Layout, dtypes, stride and ddof as
+ * lcp_fused_ws.  lcp_out ([K][H-1][W-1], out_dtype F32 or F16) and mask (as
+ * lcp_fused_ws, or NULL) may be host or device memory: the map and mask are
+ * computed into device staging at the head of `workspace` and copied into
+ * them on `stream` (asynchronously when they are pinned or device memory).
+ * workspace: device, 256-byte aligned, lcp_fused_host_workspace_bytes(M, H,
+ * W, K, out_dtype, mask != NULL) bytes for the largest bands (a smaller one
+ * gives smaller bands, as lcp_fused_ws; it must exceed the staging).  The
+ * members must stay unchanged, and the outputs must not be read, until the
+ * work on `stream` is complete.  Calls sharing one workspace must not overlap.
+ */
+size_t lcp_fused_host_workspace_bytes(int M, int H, int W, int K, lcp_dtype out_dtype, int with_mask);
+lcp_status lcp_fused_host(const void* u, const void* v, lcp_dtype in_dtype, int M, int H, int W,
+                          int64_t member_stride, int ddof, double dx, double dy, const float* iso, int K,
+                          void* lcp_out, lcp_dtype out_dtype, uint32_t* mask, void* workspace,
+                          size_t workspace_bytes, lcp_stream_t stream);
+
+/*
  * Batched closed form: many fields of uneven size (each its own H, W, M,
  * spacing and isovalue list) evaluated by ONE persistent kernel launch.  The
  * computation per field is exactly lcp_fused's (Eqs. 1-3 per vertex, the LCP of

@@ -144,6 +144,9 @@ _SIGNATURES = {
                              c_u32, c_vp, c_vp]),
     "lcp_fused_static_ws": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double, c_fp,
                                     c_int, c_vp, c_int, c_vp, c_vp]),
+    "lcp_fused_host_workspace_bytes": (ctypes.c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int]),
+    "lcp_fused_host": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_int, c_double, c_double, c_fp, c_int,
+                               c_vp, c_int, c_vp, c_vp, ctypes.c_size_t, c_vp]),
     "lcp_set_wait_budget": (ctypes.c_longlong, [ctypes.c_longlong]),
     "lcp_strip_plan": (c_int, [c_int, c_int, c_int] + [ctypes.POINTER(c_int)] * 4),
     "lcp_lpt_assign": (c_int, [ctypes.POINTER(c_i64), c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_i64)]),
@@ -524,16 +527,14 @@ _STAGING = {}
 
 def lcp_fused_host(u_host, v_host, isovalues, dx: float = 1.0, dy: float = 1.0, ddof: int = 1,
                    out_host=None, mask_host=None, device="cuda"):
-    """End-to-end call for host-resident ensembles [M, H, W] (fp32 or bf16).
-    Pinned members are read in place by the statistics kernel of
-    ``lcp_fused_ws`` over the CPU-GPU link, each byte once, with no staging
-    copy (torch's pinned memory comes from cudaHostAlloc, whose pointers a
-    kernel may use directly under unified addressing); pageable ones are first
-    copied into a device staging buffer.  The
-    LCP map (and the mask words, if ``mask_host`` is given) is copied back into
-    the host outputs (pinned ones asynchronously), all on the current stream.
-    Returns (out_host, mask_host); the results are complete, and the members
-    may be changed again, once the stream is synchronised."""
+    """End-to-end call for host-resident ensembles [M, H, W] (fp32 or bf16),
+    through the C entry point ``lcp_fused_host``: pinned members are read in
+    place by the statistics kernel over the CPU-GPU link, each byte once, and
+    the LCP map (and the mask words, if ``mask_host`` is given) is copied by the
+    library into the host outputs, all on the current stream.  Pageable members
+    (which the device cannot address) are first copied into device buffers
+    here.  Returns (out_host, mask_host); the results are complete, and the
+    members may be changed again, once the stream is synchronised."""
     if u_host.is_cuda or v_host.is_cuda:
         raise ValueError("lcp_fused_host takes host tensors")
     if u_host.dim() != 3 or u_host.shape != v_host.shape or u_host.dtype != v_host.dtype:
@@ -546,35 +547,34 @@ def lcp_fused_host(u_host, v_host, isovalues, dx: float = 1.0, dy: float = 1.0, 
     if dev.index is None:
         dev = torch.device("cuda", torch.cuda.current_device())
     in_place = u_host.is_pinned() and v_host.is_pinned()
-    slot = (str(dev), torch.cuda.current_stream(dev).cuda_stream)
-    key = (tuple(u_host.shape), u_host.dtype, k, mask_host is not None, in_place)
-    cached = _STAGING.get(slot)
-    if cached is None or cached[0] != key:
-        cached = (key, (None if in_place else torch.empty_like(u_host, device=dev),
-                        None if in_place else torch.empty_like(v_host, device=dev),
-                        torch.empty((k, h - 1, w - 1), dtype=torch.float32, device=dev),
-                        torch.empty((k, h - 1, mask_words_per_row(w)), dtype=torch.int32, device=dev)
-                        if mask_host is not None else None))
-        _STAGING[slot] = cached
-    ud, vd, od, md = cached[1]
+    if out_host is None:
+        out_host = torch.empty((k, h - 1, w - 1), dtype=torch.float32, pin_memory=True)
+    if tuple(out_host.shape) != (k, h - 1, w - 1) or out_host.dtype != torch.float32 or not out_host.is_contiguous():
+        raise ValueError("out_host must be a contiguous fp32 [K, H-1, W-1] tensor")
+    if mask_host is not None and (tuple(mask_host.shape) != (k, h - 1, mask_words_per_row(w))
+                                  or mask_host.dtype != torch.int32 or not mask_host.is_contiguous()):
+        raise ValueError("mask_host must be a contiguous int32 [K, H-1, ceil((W-1)/32)] tensor")
     if in_place:
-        lib = load()
-        code = _dtype_code(u_host.dtype)
-        need = int(lib.lcp_fused_workspace_bytes(m, h, w, code))
-        with torch.cuda.device(dev):
-            _, ws_ptr = _workspace(need, dev)
-            _check(lib.lcp_fused_ws(c_vp(u_host.data_ptr()), c_vp(v_host.data_ptr()), code, m, h, w, h * w, ddof,
-                                    float(dx), float(dy), iso_p, k, _ptr(od), LCP_F32, _ptr(md), c_vp(ws_ptr), need,
-                                    _stream()))
-    else:
+        ud, vd = u_host, v_host
+    else:  # device staging of pageable members, kept per device and stream
+        slot = (str(dev), torch.cuda.current_stream(dev).cuda_stream)
+        key = (tuple(u_host.shape), u_host.dtype)
+        cached = _STAGING.get(slot)
+        if cached is None or cached[0] != key:
+            cached = (key, (torch.empty_like(u_host, device=dev), torch.empty_like(v_host, device=dev)))
+            _STAGING[slot] = cached
+        ud, vd = cached[1]
         ud.copy_(u_host, non_blocking=True)
         vd.copy_(v_host, non_blocking=True)
-        lcp_fused_ws(ud, vd, iso, dx, dy, ddof, mask=md is not None, out=od, mask_out=md)
-    if out_host is None:
-        out_host = torch.empty(od.shape, dtype=od.dtype, pin_memory=True)
-    out_host.copy_(od, non_blocking=True)
-    if mask_host is not None:
-        mask_host.copy_(md, non_blocking=True)
+    lib = load()
+    code = _dtype_code(u_host.dtype)
+    need = int(lib.lcp_fused_host_workspace_bytes(m, h, w, k, LCP_F32, int(mask_host is not None)))
+    with torch.cuda.device(dev):
+        _, ws_ptr = _workspace(need, dev)
+        _check(lib.lcp_fused_host(c_vp(ud.data_ptr()), c_vp(vd.data_ptr()), code, m, h, w, h * w, ddof, float(dx),
+                                  float(dy), iso_p, k, c_vp(out_host.data_ptr()), LCP_F32,
+                                  c_vp(mask_host.data_ptr()) if mask_host is not None else None, c_vp(ws_ptr), need,
+                                  _stream()))
     return out_host, mask_host
 
 

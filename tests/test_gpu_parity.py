@@ -437,6 +437,55 @@ def test_fused_ws_ocean_8192_bf16_sampled(lib):
     torch.cuda.empty_cache()
 
 
+def test_fused_host_c_abi_host_and_device_outputs(lib):
+    """lcp_fused_host called through the C ABI: pinned members read in place,
+    the map copied into pageable host memory and into device memory, fp16
+    maps, a workspace below the largest bands (smaller bands), all equal to
+    lcp_fused_ws bit for bit; pageable members are rejected before any work."""
+    import ctypes
+
+    clib = lib.load()
+    h, w, m = 61, 97, 7
+    d = _fields(h, w, m, seed=23, k=3)
+    iso = d["isovalues"]
+    k = len(iso)
+    u, v = torch.from_numpy(d["u"]), torch.from_numpy(d["v"])
+    ref, ref_mask = lib.lcp_fused_ws(u.cuda(), v.cuda(), iso, mask=True)
+    ref16, _ = lib.lcp_fused_ws(u.cuda(), v.cuda(), iso, out_dtype=torch.float16)
+    uh, vh = u.pin_memory(), v.pin_memory()
+    iso_c = (ctypes.c_float * k)(*[float(c) for c in iso])
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call(uu, vv, out, out_code, mask, ws_bytes):
+        ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device="cuda")
+        p = ws.data_ptr() + (-ws.data_ptr()) % 256
+        r = clib.lcp_fused_host(ctypes.c_void_p(uu.data_ptr()), ctypes.c_void_p(vv.data_ptr()), 0, m, h, w, h * w, 1,
+                                1.0, 1.0, iso_c, k, ctypes.c_void_p(out.data_ptr()), out_code,
+                                ctypes.c_void_p(mask.data_ptr()) if mask is not None else None, ctypes.c_void_p(p),
+                                ws_bytes, st)
+        torch.cuda.synchronize()
+        return r
+
+    need = clib.lcp_fused_host_workspace_bytes(m, h, w, k, 0, 1)
+    out = torch.full((k, h - 1, w - 1), float("nan"))  # pageable host output
+    mask = torch.full(tuple(ref_mask.shape), -1, dtype=torch.int32)
+    assert call(uh, vh, out, 0, mask, need) == 0, clib.lcp_last_error()
+    assert torch.equal(out, ref.cpu()) and torch.equal(mask, ref_mask.cpu())
+    outd = torch.full_like(ref, float("nan"))  # device output
+    assert call(uh, vh, outd, 0, None, clib.lcp_fused_host_workspace_bytes(m, h, w, k, 0, 0)) == 0
+    assert torch.equal(outd, ref)
+    out16 = torch.empty((k, h - 1, w - 1), dtype=torch.float16).pin_memory()
+    assert call(uh, vh, out16, 2, None, clib.lcp_fused_host_workspace_bytes(m, h, w, k, 2, 0)) == 0
+    assert torch.equal(out16, ref16.cpu())
+    small = need - clib.lcp_fused_workspace_bytes(m, h, w, 0) + lib.lcp_fused_workspace_bytes(m, h, w) // 2 + 512
+    assert 8 <= lib.lcp_fused_band_rows(h, w, small - (need - clib.lcp_fused_workspace_bytes(m, h, w, 0))) < h - 1
+    out.fill_(float("nan"))
+    assert call(uh, vh, out, 0, mask, small) == 0
+    assert torch.equal(out, ref.cpu()) and torch.equal(mask, ref_mask.cpu())
+    assert call(u, v, out, 0, None, need) == -1 and "pinned" in clib.lcp_last_error().decode()
+    assert lib.lcp_device_status(reset=True) == 0
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_fused_host_pinned_in_place_and_pageable_staged(lib, dtype):
     """lcp_fused_host: pinned members read in place by the statistics kernel,

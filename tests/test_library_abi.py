@@ -257,3 +257,27 @@ def test_volume_ring_and_contour_workspace_sizes(clib):
         n = wsc(m, h, w)
         assert n >= 264 and (n - 256) % 8 == 0 and n > prev  # header + one 8-byte descriptor per tile
         prev = n
+
+
+def test_fused_host_rejects_bad_arguments_and_sizes_its_workspace(clib):
+    """lcp_fused_host: host-side checks before any device work, and its
+    workspace = the map and mask staging (each rounded up to 256 bytes) plus
+    lcp_fused_ws's records (host arithmetic only)."""
+    iso = (ctypes.c_float * 2)(0.0, 1.0)
+    f = clib.lcp_fused_host
+    head = [FAKE, FAKE, 0, 4, 8, 8, 64, 1, 1.0, 1.0, iso, 2]
+    ws = ctypes.c_void_p(512)
+    assert f(*head, None, 0, None, ws, 1 << 30, None) == -1 and "NULL output" in _err(clib)
+    assert f(*head, FAKE, 3, None, ws, 1 << 30, None) == -1 and "out dtype" in _err(clib)  # F64
+    assert f(*head, FAKE, 0, None, None, 1 << 30, None) == -1 and "workspace" in _err(clib)
+    assert f(*head, FAKE, 0, None, ctypes.c_void_p(520), 1 << 30, None) == -1 and "aligned" in _err(clib)
+    bad = list(head)
+    bad[6] = 63  # member stride below H * W
+    assert f(*bad, FAKE, 0, None, ws, 1 << 30, None) == -1 and "member_stride" in _err(clib)
+    size = clib.lcp_fused_host_workspace_bytes
+    records = clib.lcp_fused_workspace_bytes(4, 8, 8, 0)
+    # K = 2 maps of 7 x 7 fp32 cells = 392 B -> 512; mask words 2 x 7 x 1 x 4 = 56 B -> 256
+    assert size(4, 8, 8, 2, 0, 0) == 512 + records
+    assert size(4, 8, 8, 2, 0, 1) == 512 + 256 + records
+    assert size(4, 8, 8, 2, 2, 0) == 256 + records  # fp16 maps: 196 B -> 256
+    assert size(4, 1, 8, 2, 0, 0) == 0 and size(4, 8, 8, 0, 0, 0) == 0
