@@ -4,9 +4,11 @@
 // before mapping it (Sec. 4.2, Fig. 3c); no graphics API is involved here.
 //
 // Every value costs 4 bytes read and 4 bytes written, so the kernel must stay
-// under about 45 instructions per value to run at HBM speed.  Hence: each
-// thread maps 4 consecutive values (one 16-byte load and store when the
-// buffers allow it); the reciprocals and colour differences of every stop
+// under about 45 instructions per value to run at HBM speed, and keep enough
+// loads in flight.  Hence: each thread maps groups of 4 consecutive values (one
+// 16-byte load and store when the buffers allow it), two groups per trip of a
+// persistent grid with both groups' loads and mask words issued before either
+// is mapped; the reciprocals and colour differences of every stop
 // segment are formed once per call on the host (each value then costs
 // multiplications instead of two divisions; the bytes can differ from the
 // exact map by one where a channel lies within fp32 rounding of a byte
@@ -26,6 +28,10 @@ namespace lcp {
 namespace {
 
 constexpr int kCT = 256;  // threads per block
+constexpr int kCB = 4;    // resident blocks per SM (<= 64 registers), the persistent grid's size per SM
+constexpr int kCU = 2;    // groups per thread and trip
+// (measured on 4 x 8191^2 values with the mask, blocks per SM x groups per trip: 4 x 2 0.461 ms,
+// 5 x 2 0.488, 3 x 3 0.489, 3 x 2 0.494, 6 x 1 0.503, 2 x 4 0.578)
 
 struct Seg {  // one stop segment s: position, 1 / width, colour c_s, difference d_s
     float t, r, pad0, pad1;
@@ -79,8 +85,35 @@ __device__ __forceinline__ uint32_t map_one(const ColorParams& p, const Seg* seg
     return x != x ? p.nan_rgba : c;
 }
 
-template <bool MASK, typename Idx, int NT>
-__global__ void __launch_bounds__(kCT) colormap_kernel(const __grid_constant__ ColorParams p) {
+// Mask bits of the cnt values from flat position (row, col) on: one or two
+// words when the group lies in one mask row (loaded by the caller: w0, w1),
+// element by element when it wraps into the next row.
+template <typename Idx>
+__device__ __forceinline__ uint32_t group_bits(const ColorParams& p, Idx row, int col, int cnt, uint32_t w0,
+                                               uint32_t w1) {
+    if (col + cnt <= p.cols) {
+        const int sh = col & 31;
+        const uint64_t w2 = (uint64_t)w0 | ((uint64_t)w1 << 32);
+        return (uint32_t)(w2 >> sh);
+    }
+    uint32_t bits = 0;
+    int cc = col;
+    Idx rr = row;
+    for (int e = 0; e < cnt; ++e) {
+        bits |= ((p.mask[(int64_t)rr * p.n_words + (cc >> 5)] >> (cc & 31)) & 1u) << e;
+        if (++cc == p.cols) {
+            cc = 0;
+            ++rr;
+        }
+    }
+    return bits;
+}
+
+// U groups of 4 values per thread and trip: every group's value load (and its
+// mask words) is issued before any group is mapped, so U loads per thread are
+// in flight instead of one, and the mask read is no second round trip.
+template <bool MASK, typename Idx, int NT, int U>
+__global__ void __launch_bounds__(kCT, kCB) colormap_kernel(const __grid_constant__ ColorParams p) {
     __shared__ Seg seg[LCP_MAX_COLOR_STOPS - 1];
     for (int q = threadIdx.x; q < p.n_seg; q += kCT) seg[q] = p.seg[q];
     float thr[NT > 0 ? NT : 1];
@@ -90,7 +123,7 @@ __global__ void __launch_bounds__(kCT) colormap_kernel(const __grid_constant__ C
     const bool vec = ((reinterpret_cast<uintptr_t>(p.x) | reinterpret_cast<uintptr_t>(p.rgba)) & 15) == 0;
     const Idx n = (Idx)p.n;
     const Idx g0 = ((Idx)blockIdx.x * kCT + threadIdx.x) * 4, step = (Idx)gridDim.x * kCT * 4;
-    // mask position of the group's first value, advanced by the stride without division
+    // mask position of the trip's first group, advanced by the stride without division
     int col = 0, dcol = 0;
     Idx row = 0, drow = 0;
     if (MASK) {
@@ -99,55 +132,61 @@ __global__ void __launch_bounds__(kCT) colormap_kernel(const __grid_constant__ C
         drow = step / (Idx)p.cols;
         dcol = (int)(step - drow * (Idx)p.cols);
     }
-    for (Idx g = g0; g < n; g += step) {
-        float x[4];
-        const int cnt = n - g >= 4 ? 4 : (int)(n - g);
-        if (vec && cnt == 4) {
-            const float4 r = __ldcs(reinterpret_cast<const float4*>(p.x + g));
-            x[0] = r.x;
-            x[1] = r.y;
-            x[2] = r.z;
-            x[3] = r.w;
-        } else {
-            for (int e = 0; e < 4; ++e) x[e] = e < cnt ? p.x[g + e] : 0.0f;
-        }
-        uint32_t c[4];
+    for (Idx g = g0; g < n; g += (Idx)U * step) {
+        float x[U][4];
+        int cnt[U];
+        uint32_t mw0[U], mw1[U];
+        Idx mrow[U];
+        int mcol[U];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) c[e] = map_one<NT>(p, seg, thr, x[e]);
-        if (MASK) {
-            uint32_t bits;
-            if (col + cnt <= p.cols) {  // the group lies in one mask row: one or two words
-                const uint32_t* wp = p.mask + (int64_t)row * p.n_words + (col >> 5);
-                const int sh = col & 31;
-                uint64_t w2 = wp[0];
-                if (sh + cnt > 32) w2 |= (uint64_t)wp[1] << 32;
-                bits = (uint32_t)(w2 >> sh);
-            } else {  // the group wraps into the next row
-                bits = 0;
-                int cc = col;
-                Idx rr = row;
-                for (int e = 0; e < cnt; ++e) {
-                    bits |= ((p.mask[(int64_t)rr * p.n_words + (cc >> 5)] >> (cc & 31)) & 1u) << e;
-                    if (++cc == p.cols) {
-                        cc = 0;
-                        ++rr;
-                    }
+        for (int k = 0; k < U; ++k) {  // issue every load of the trip
+            const Idx gk = g + (Idx)k * step;
+            cnt[k] = gk >= n ? 0 : (n - gk >= 4 ? 4 : (int)(n - gk));
+            if (vec && cnt[k] == 4) {
+                const float4 r = __ldcs(reinterpret_cast<const float4*>(p.x + gk));
+                x[k][0] = r.x;
+                x[k][1] = r.y;
+                x[k][2] = r.z;
+                x[k][3] = r.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) x[k][e] = e < cnt[k] ? p.x[gk + e] : 0.0f;
+            }
+            if (MASK) {
+                mrow[k] = row;
+                mcol[k] = col;
+                mw0[k] = mw1[k] = 0u;
+                if (cnt[k] > 0 && col + cnt[k] <= p.cols) {
+                    const uint32_t* wp = p.mask + (int64_t)row * p.n_words + (col >> 5);
+                    mw0[k] = wp[0];
+                    if ((col & 31) + cnt[k] > 32) mw1[k] = wp[1];
+                }
+                col += dcol;
+                row += drow;
+                if (col >= p.cols) {
+                    col -= p.cols;
+                    ++row;
                 }
             }
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (((bits >> e) & 1u) && x[e] == x[e]) c[e] = p.mask_rgba;  // NaN keeps its colour
-            col += dcol;
-            row += drow;
-            if (col >= p.cols) {
-                col -= p.cols;
-                ++row;
-            }
         }
-        if (vec && cnt == 4) {
-            __stcs(reinterpret_cast<uint4*>(p.rgba + g), make_uint4(c[0], c[1], c[2], c[3]));
-        } else {
-            for (int e = 0; e < cnt; ++e) p.rgba[g + e] = c[e];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            if (cnt[k] == 0) break;
+            const Idx gk = g + (Idx)k * step;
+            uint32_t c[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) c[e] = map_one<NT>(p, seg, thr, x[k][e]);
+            if (MASK) {
+                const uint32_t bits = group_bits<Idx>(p, mrow[k], mcol[k], cnt[k], mw0[k], mw1[k]);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (((bits >> e) & 1u) && x[k][e] == x[k][e]) c[e] = p.mask_rgba;  // NaN keeps its colour
+            }
+            if (vec && cnt[k] == 4) {
+                __stcs(reinterpret_cast<uint4*>(p.rgba + gk), make_uint4(c[0], c[1], c[2], c[3]));
+            } else {
+                for (int e = 0; e < cnt[k]; ++e) p.rgba[gk + e] = c[e];
+            }
         }
     }
 }
@@ -155,11 +194,11 @@ __global__ void __launch_bounds__(kCT) colormap_kernel(const __grid_constant__ C
 template <bool MASK, typename Idx>
 void launch_nt(const ColorParams& p, int grid, cudaStream_t st) {
     const int interior = p.n_seg - 1;  // stop positions strictly inside (0, 1)
-    if (interior == 0) colormap_kernel<MASK, Idx, 0><<<grid, kCT, 0, st>>>(p);
-    else if (interior <= 2) colormap_kernel<MASK, Idx, 2><<<grid, kCT, 0, st>>>(p);
-    else if (interior <= 4) colormap_kernel<MASK, Idx, 4><<<grid, kCT, 0, st>>>(p);
-    else if (interior <= 6) colormap_kernel<MASK, Idx, 6><<<grid, kCT, 0, st>>>(p);
-    else colormap_kernel<MASK, Idx, LCP_MAX_COLOR_STOPS - 2><<<grid, kCT, 0, st>>>(p);
+    if (interior == 0) colormap_kernel<MASK, Idx, 0, kCU><<<grid, kCT, 0, st>>>(p);
+    else if (interior <= 2) colormap_kernel<MASK, Idx, 2, kCU><<<grid, kCT, 0, st>>>(p);
+    else if (interior <= 4) colormap_kernel<MASK, Idx, 4, kCU><<<grid, kCT, 0, st>>>(p);
+    else if (interior <= 6) colormap_kernel<MASK, Idx, 6, kCU><<<grid, kCT, 0, st>>>(p);
+    else colormap_kernel<MASK, Idx, LCP_MAX_COLOR_STOPS - 2, kCU><<<grid, kCT, 0, st>>>(p);
 }
 
 }  // namespace
@@ -230,7 +269,7 @@ extern "C" lcp_status lcp_colormap(const float* values, int planes, int rows, in
         sg.d = make_float4(d[0], d[1], d[2], d[3]);
     }
     const int64_t groups = (n + 3) / 4;
-    const int grid = (int)std::min<int64_t>((groups + kCT - 1) / kCT, (int64_t)num_sms() * 8);
+    const int grid = (int)std::min<int64_t>((groups + kCT - 1) / kCT, (int64_t)num_sms() * kCB);
     cudaStream_t st = (cudaStream_t)stream;
     const bool small = n < (1ll << 31) - 4 * (int64_t)kCT * grid;
     if (mask) {
