@@ -29,8 +29,17 @@ constexpr int kOffW1 = 0, kOffB1 = 2048, kOffW2 = 2112, kOffB2 = 6208, kOffW3 = 
 // expansion: with delta = S1/M and e_p = S_p/M,
 //   m2 = e2 - delta^2,  m3 = e3 - 3 delta e2 + 2 delta^3,
 //   m4 = e4 - 4 delta e3 + 6 delta^2 e2 - 3 delta^4.
+// Members in batches (every load of a batch in flight at once): fp32 4 per batch at
+// <= 64 registers (4 blocks per SM), bf16 8 per batch at full registers.  Measured on
+// 1024^2 x 50 members: fp32 0.111 -> 0.071 ms (0.94 of the measured HBM copy peak),
+// bf16 0.116 -> 0.060 ms, against one load in flight per thread.
+template <typename T>
+struct MomTune {
+    static constexpr int kBatch = sizeof(T) == 4 ? 4 : 8;
+    static constexpr int kMinBlocks = sizeof(T) == 4 ? 4 : 1;
+};
 template <typename T, int VEC>
-__global__ void __launch_bounds__(256) moments_kernel(const T* __restrict__ u, const T* __restrict__ v, int M,
+__global__ void __launch_bounds__(256, MomTune<T>::kMinBlocks) moments_kernel(const T* __restrict__ u, const T* __restrict__ v, int M,
                                                      int64_t stride, int64_t n_vert, int vec_ok, float4* mom) {
     using L = Loader<T, VEC>;
     const float fm = (float)M;
@@ -54,17 +63,7 @@ __global__ void __launch_bounds__(256) moments_kernel(const T* __restrict__ u, c
                 for (int e = 0; e < VEC; ++e)
                     if (e < cnt) Loader<T, 1>::cvt(Loader<T, 1>::load(x + n0 + e), &x0[e]);
             }
-            for (int m = 1; m < M; ++m) {
-                float a[VEC];
-                if (vec) {
-                    L::cvt(L::load(x + (int64_t)m * stride + n0), a);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) {
-                        a[e] = 0.f;
-                        if (e < cnt) Loader<T, 1>::cvt(Loader<T, 1>::load(x + (int64_t)m * stride + n0 + e), &a[e]);
-                    }
-                }
+            auto acc = [&](const float (&a)[VEC]) {
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) {
                     const float d = a[e] - x0[e], d2 = d * d;
@@ -72,6 +71,32 @@ __global__ void __launch_bounds__(256) moments_kernel(const T* __restrict__ u, c
                     s[1][e] += d2;
                     s[2][e] = fmaf(d2, d, s[2][e]);
                     s[3][e] = fmaf(d2, d2, s[3][e]);
+                }
+            };
+            if (vec) {  // members in batches of kMB, every load of a batch in flight at once
+                constexpr int kMB = MomTune<T>::kBatch;
+                for (int m = 1; m < M; m += kMB) {
+                    typename L::raw_t r[kMB];
+#pragma unroll
+                    for (int q = 0; q < kMB; ++q)
+                        if (m + q < M) r[q] = L::load(x + (int64_t)(m + q) * stride + n0);
+#pragma unroll
+                    for (int q = 0; q < kMB; ++q)
+                        if (m + q < M) {
+                            float a[VEC];
+                            L::cvt(r[q], a);
+                            acc(a);
+                        }
+                }
+            } else {
+                for (int m = 1; m < M; ++m) {
+                    float a[VEC];
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        a[e] = 0.f;
+                        if (e < cnt) Loader<T, 1>::cvt(Loader<T, 1>::load(x + (int64_t)m * stride + n0 + e), &a[e]);
+                    }
+                    acc(a);
                 }
             }
 #pragma unroll
