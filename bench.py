@@ -192,20 +192,23 @@ def profiled_traffic(profile="lcp_fused_ws_latlon_721x1440_m51_k8.md", sources=(
 
 
 # ---------------------------------------------------------------------------
-def crop_accuracy(lcp, get_crop, H, W, iso, crops, dx=1.0, dy=1.0):
+def crop_accuracy(lcp, get_crop, H, W, iso, crops, dx=1.0, dy=1.0, oracle_fn=None, halo=1):
     """Max |GPU - FP64 oracle| of the LCP on crops of the field.  Each crop
-    (r0, r1, c0, c1) of vertices is evaluated by the oracle as a grid of its
-    own; cell rows and columns next to a crop edge that is not a grid edge
-    are dropped (their stencils reach outside the crop).  get_crop(r0, r1, c0,
-    c1) returns fp32 numpy (u, v) [M, r1-r0, c1-c0]."""
+    (r0, r1, c0, c1) of vertices is evaluated by the oracle (``oracle_fn``,
+    default the closed form) as a grid of its own; ``halo`` cell rows and
+    columns next to a crop edge that is not a grid edge are dropped (their
+    stencils reach outside the crop: 1 for Eqs. 2/3, 2 for the speed gradient,
+    whose members are themselves a stencil).  get_crop(r0, r1, c0, c1) returns
+    fp32 numpy (u, v) [M, r1-r0, c1-c0]."""
     import oracle as O
 
+    fn = oracle_fn or O.lcp_closed_form
     worst, cells = 0.0, 0
     for (r0, r1, c0, c1) in crops:
         u, v = get_crop(r0, r1, c0, c1)
-        ref = O.lcp_closed_form(u, v, dx, dy, iso)["lcp"]
-        a, b = (1 if r0 > 0 else 0), ref.shape[1] - (1 if r1 < H else 0)
-        cA, cB = (1 if c0 > 0 else 0), ref.shape[2] - (1 if c1 < W else 0)
+        ref = fn(u, v, dx, dy, iso)["lcp"]
+        a, b = (halo if r0 > 0 else 0), ref.shape[1] - (halo if r1 < H else 0)
+        cA, cB = (halo if c0 > 0 else 0), ref.shape[2] - (halo if c1 < W else 0)
         got = lcp[:, r0 + a:r0 + b, c0 + cA:c0 + cB].float().cpu().numpy()
         worst = max(worst, float(np.max(np.abs(got - ref[:, a:b, cA:cB]))))
         cells += got.shape[1] * got.shape[2]
@@ -544,6 +547,26 @@ def batch_cpu_baseline(fields, budget_s=12.0):
             "seconds": round(dt, 2)}
 
 
+def batch_accuracy(fields, outs, n_check=4):
+    """Max |GPU - FP64 oracle| over the whole maps of the n_check smallest fields
+    of the batch (the maps are fp16, so the error includes the fp16 rounding of
+    values in [0, 1], at most 2^-12)."""
+    import oracle as O
+
+    order = sorted(range(len(fields)), key=lambda i: fields[i]["u"].shape[1] * fields[i]["u"].shape[2])[:n_check]
+    worst, cells = 0.0, 0
+    for i in order:
+        f = fields[i]
+        ref = O.lcp_closed_form(f["u"].float().cpu().numpy(), f["v"].float().cpu().numpy(), 1.0, 1.0,
+                                np.asarray(f["isovalues"], np.float32))["lcp"]
+        got = outs[i].float().cpu().numpy()
+        worst = max(worst, float(np.max(np.abs(got - ref))))
+        cells += ref.shape[1] * ref.shape[2]
+    return {"max_abs_err_vs_fp64_oracle": worst, "bound": "fp16 rounding of values in [0, 1] (2^-12) plus the fp32 path's error (< 1e-5)",
+            "cells_checked": cells,
+            "fields_checked": [list(fields[i]["u"].shape) for i in order]}
+
+
 def batch_arm(args):
     """256 uneven fields per step, one persistent graph-captured launch; each rank its own batch."""
     import torch
@@ -613,6 +636,7 @@ def batch_arm(args):
             "peak_kind": peak_kind, "kernel": f"batch_kernel<float,half,{best[0]},{best[1]}> (persistent)",
             "alg_bytes_per_launch": alg, "kernel_ms": round(kern_ms, 4)}
     cpu = batch_cpu_baseline(fields) if (not args.no_cpu and rank == 0 and world == 1) else None
+    accuracy = batch_accuracy(fields, b.lcp) if (not args.no_cpu and rank == 0) else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": args.warmup,
@@ -626,7 +650,7 @@ def batch_arm(args):
                        "l2": f"no flush: inputs {plan.member_bytes / 1e9:.1f} GB > 129 MB L2",
                        "lcp_values_per_s": world * plan.cell_isovalues / (ms_per_step / 1e3),
                        "hbm_frac_of_measured": roof["frac"]},
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "cpu_baseline": cpu, "accuracy": accuracy,
             "e2e": None, "e2e_note": "not measured for the batch: its 59 GB of members would have to be pinned on the host",
             "clocks": clocks.summary(t_wall0, t_wall1), "gpu_launches": n,  # one persistent kernel per step
             "gpu": torch.cuda.get_device_name(dev),
@@ -1095,7 +1119,8 @@ def redsea_arm(args):
     def step():
         lib.lcp_speed_gradient_ws(u, v, iso, 1.0, 1.0, 1, out=out)
 
-    total_ms, kern_ms, clocks = timed_steps(torch, step, args.steps, args.warmup, local, pg, dev)
+    block_ms, blk, clocks = timed_blocks(torch, step, args.steps, args.warmup, local, pg, dev)
+    total_ms, kern_ms = block_ms, blk["block_ms_median"] / args.steps  # one block of steps; per step
     n = args.steps
     ms_per_step = total_ms / n
     value = weak_scaling_value(Hc * Wc, world, ms_per_step)
@@ -1133,6 +1158,16 @@ def redsea_arm(args):
                    "max_abs_diff_vs_fused": float(torch.max(torch.abs(two - out)).item())}
         del two
         torch.cuda.empty_cache()
+    accuracy = None
+    if rank == 0:  # the map of the last timed step on three crops (the oracle sees the same bf16-rounded members)
+        import oracle as O
+
+        cw = min(Ww, 1024)
+        accuracy = crop_accuracy(out, lambda r0, r1, c0, c1: (u[:, r0:r1, c0:c1].float().cpu().numpy(),
+                                                              v[:, r0:r1, c0:c1].float().cpu().numpy()),
+                                 Hh, Ww, iso, [(0, 24, 0, cw), (Hh // 2 - 12, Hh // 2 + 12, Ww - cw, Ww),
+                                               (Hh - 24, Hh, (Ww - cw) // 2, (Ww - cw) // 2 + cw)],
+                                 oracle_fn=O.speed_gradient_lcp, halo=2)
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         import oracle as O
@@ -1156,10 +1191,11 @@ def redsea_arm(args):
                    "W": Ww, "M": Mm, "K": Kk, "isovalues": [float(c) for c in iso], "global_batch": world,
                    "parallelism": f"independent fields x{world}" if world > 1 else "single",
                    "l2": f"no flush: inputs {2 * Mm * Hh * Ww * 2 / 1e9:.1f} GB > 129 MB L2",
-                   "lcp_values_per_s": value * Kk, "hbm_frac_of_measured": roof["frac"]},
-        "roofline": roof, "unfused": unfused, "cpu_baseline": cpu, "e2e": None,
+                   "lcp_values_per_s": value * Kk, "hbm_frac_of_measured": roof["frac"], "timing": blk},
+        "roofline": roof, "unfused": unfused, "cpu_baseline": cpu, "e2e": None, "accuracy": accuracy,
         "e2e_note": "not measured for this line: 5.4 GB of members per step would be pinned on the host",
-        "clocks": clocks, "gpu_launches": 2 * ws_row_bands(lib, Mm, Hh, Ww) * n, "gpu": torch.cuda.get_device_name(dev),
+        "clocks": clocks, "gpu_launches": 2 * ws_row_bands(lib, Mm, Hh, Ww) * n * blk["blocks"],
+        "gpu": torch.cuda.get_device_name(dev),
     }
     return _finish(torch, pg, line, rank)
 
@@ -1184,7 +1220,8 @@ def colormap_arm(args):
     def step():
         lib.lcp_colormap(lcp, 0.0, 1.0, mask=mask, out=rgba)
 
-    total_ms, kern_ms, clocks = timed_steps(torch, step, args.steps, args.warmup, local, pg, dev)
+    block_ms, blk, clocks = timed_blocks(torch, step, args.steps, args.warmup, local, pg, dev)
+    total_ms, kern_ms = block_ms, blk["block_ms_median"] / args.steps  # one block of steps; per step
     n = args.steps
     ms_per_step = total_ms / n
     values = Kk * Hc * Wc
@@ -1197,6 +1234,20 @@ def colormap_arm(args):
             "traffic": profiled_traffic("lcp_colormap_4x8191x8191.md", ("colormap.cu", "lcp_common.cuh")),
             "peak_kind": peak_kind, "kernel": "colormap_kernel<mask,uint32>", "alg_bytes_per_launch": alg,
             "kernel_ms": round(kern_ms, 4)}
+    accuracy = None
+    if rank == 0:  # bytes of the last timed image against the FP64 oracle on three bands of rows
+        from oracle import viz as V
+
+        diff_max, n_diff, n_bytes = 0, 0, 0
+        for k, j0 in ((0, 0), (Kk // 2, Hc // 2), (Kk - 1, max(0, Hc - 16))):
+            x = lcp[k, j0:j0 + 16].cpu().numpy()
+            bits = lib.unpack_mask(mask[k:k + 1, j0:j0 + 16], Wc + 1)[0].cpu().numpy()
+            ref = V.colormap_rgba(x, 0.0, 1.0, lib.DEFAULT_STOPS, mask=bits, mask_rgba=0xFF000000).astype(np.int64)
+            got = rgba[k, j0:j0 + 16].cpu().numpy().astype(np.int64)
+            dd = np.abs(got - ref)
+            diff_max, n_diff, n_bytes = max(diff_max, int(dd.max())), n_diff + int(np.count_nonzero(dd)), n_bytes + dd.size
+        accuracy = {"max_abs_byte_diff_vs_fp64_oracle": diff_max, "bytes_differing": n_diff, "bytes_checked": n_bytes,
+                    "note": "a byte may differ by one where the channel lies within fp32 rounding of a byte boundary"}
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         from oracle import viz as V
@@ -1222,16 +1273,40 @@ def colormap_arm(args):
                    "planes": Kk, "rows": Hc, "cols": Wc, "global_batch": world,
                    "parallelism": f"independent maps x{world}" if world > 1 else "single",
                    "l2": f"no flush: input {values * 4 / 1e9:.2f} GB > 129 MB L2", "values_per_s": value * Kk,
-                   "hbm_frac_of_measured": roof["frac"]},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": None,
+                   "hbm_frac_of_measured": roof["frac"], "timing": blk},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": None, "accuracy": accuracy,
         "e2e_note": "not measured for this line: the map is produced on the device by the LCP path",
-        "clocks": clocks, "gpu_launches": n, "gpu": torch.cuda.get_device_name(dev),
+        "clocks": clocks, "gpu_launches": n * blk["blocks"], "gpu": torch.cuda.get_device_name(dev),
     }
     return _finish(torch, pg, line, rank)
 
 
 VOLUME_WORKLOAD = ("volume 256x256x256, 20 members fp32 of (u, v, w) (64 random 3D Fourier modes per component + "
                    "log-normal noise), 4 isovalues; fused 3D closed-form LCP of the hexahedral cells (fp32 maps)")
+
+
+def volume_accuracy(out, u, v, w, iso, edge=20):
+    """Max |GPU - FP64 oracle| of the 3D map on three sub-volumes (a corner, the
+    centre, the far corner) of edge^3 vertices, each evaluated by the oracle as a
+    volume of its own; cells next to a face that is not a volume face are
+    dropped (their stencils reach outside the sub-volume)."""
+    from oracle import volume as V3
+
+    M, D, H, W = u.shape
+    e = min(edge, D, H, W)
+    worst, cells = 0.0, 0
+    starts = [(0, 0, 0), ((D - e) // 2, (H - e) // 2, (W - e) // 2), (D - e, H - e, W - e)]
+    for (z0, y0, x0) in starts:
+        sl = (slice(None), slice(z0, z0 + e), slice(y0, y0 + e), slice(x0, x0 + e))
+        ref = V3.lcp_closed_form_3d(*(t[sl].float().cpu().numpy() for t in (u, v, w)), 1.0, 1.0, 1.0, iso)["lcp"]
+        lo = [1 if s0 > 0 else 0 for s0 in (z0, y0, x0)]
+        hi = [n - (1 if s0 + e < full else 0) for n, s0, full in zip(ref.shape[1:], (z0, y0, x0), (D, H, W))]
+        r = ref[:, lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]]
+        got = out[:, z0 + lo[0]:z0 + hi[0], y0 + lo[1]:y0 + hi[1], x0 + lo[2]:x0 + hi[2]].float().cpu().numpy()
+        worst = max(worst, float(np.max(np.abs(got - r))))
+        cells += r.shape[1] * r.shape[2] * r.shape[3]
+    return {"max_abs_err_vs_fp64_oracle": worst, "cells_checked": cells, "isovalues": len(iso),
+            "subvolumes": [[z0, y0, x0, e] for (z0, y0, x0) in starts]}
 
 
 def volume_arm(args):
@@ -1249,7 +1324,8 @@ def volume_arm(args):
     def step():
         lib.lcp3d_fused_ws(u, v, w, iso, out=out)
 
-    total_ms, kern_ms, clocks = timed_steps(torch, step, args.steps, args.warmup, local, pg, dev)
+    block_ms, blk, clocks = timed_blocks(torch, step, args.steps, args.warmup, local, pg, dev)
+    total_ms, kern_ms = block_ms, blk["block_ms_median"] / args.steps  # one block of steps; per step
     n = args.steps
     ms_per_step = total_ms / n
     value = weak_scaling_value(cells, world, ms_per_step)
@@ -1264,6 +1340,7 @@ def volume_arm(args):
             "peak_kind": peak_kind,
             "kernel": "lcp3d_fused_ws step: stats3_kernel<float> + lcp3_kernel<4,nomask,float> per slab of z-planes",
             "alg_bytes_per_launch": alg, "kernel_ms": round(kern_ms, 4)}
+    accuracy = volume_accuracy(out, u, v, w, iso) if rank == 0 else None
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         from oracle import volume as V3
@@ -1287,10 +1364,10 @@ def volume_arm(args):
                    "H": Hh, "W": Ww, "M": Mm, "K": Kk, "global_batch": world,
                    "parallelism": f"independent volumes x{world}" if world > 1 else "single",
                    "l2": f"no flush: inputs {3 * Mm * Dd * Hh * Ww * 4 / 1e9:.1f} GB > 129 MB L2",
-                   "lcp_values_per_s": value * Kk, "hbm_frac_of_measured": roof["frac"]},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": None,
+                   "lcp_values_per_s": value * Kk, "hbm_frac_of_measured": roof["frac"], "timing": blk},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": None, "accuracy": accuracy,
         "e2e_note": "not measured for this line: 4 GB of members per step would be pinned on the host",
-        "clocks": clocks, "gpu_launches": 2 * slabs * n, "gpu": torch.cuda.get_device_name(dev),
+        "clocks": clocks, "gpu_launches": 2 * slabs * n * blk["blocks"], "gpu": torch.cuda.get_device_name(dev),
     }
     return _finish(torch, pg, line, rank)
 
@@ -1326,7 +1403,8 @@ def contours_arm(args):
                                           B._ptr(buf[0]), B._ptr(buf[1]), total, B._ptr(count), B.c_vp(ws_ptr), nw,
                                           B._stream()))
 
-    total_ms, kern_ms, clocks = timed_steps(torch, raw_step, args.steps, args.warmup, local, pg, dev)
+    block_ms, blk, clocks = timed_blocks(torch, raw_step, args.steps, args.warmup, local, pg, dev)
+    total_ms, kern_ms = block_ms, blk["block_ms_median"] / args.steps  # one block of steps; per step
     assert int(count.item()) == total
     n = args.steps
     ms_per_step = total_ms / n
@@ -1376,7 +1454,7 @@ def contours_arm(args):
                                   "what": "lcp_contours of mu_d (lcp_stats + lcp_divergence untimed), incl. count read-back"}},
         "roofline": roof, "cpu_baseline": cpu, "e2e": None,
         "e2e_note": "not measured for this line: the segments stay on the device for drawing",
-        "clocks": clocks, "gpu_launches": n, "gpu": torch.cuda.get_device_name(dev),
+        "clocks": clocks, "gpu_launches": n * blk["blocks"], "gpu": torch.cuda.get_device_name(dev),
     }
     return _finish(torch, pg, line, rank)
 
