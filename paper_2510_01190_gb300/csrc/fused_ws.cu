@@ -33,8 +33,9 @@
 // processed in bands of rows (records of the band plus one halo row on each
 // side, then its cells), so the workspace never spills to HBM; a smaller
 // workspace than lcp_fused_workspace_bytes reports gives smaller bands.  With
-// several bands the statistics grid is persistent (3 blocks per SM), so that
-// the LCP grid runs beside each band's stream rather than after it.
+// several bands the statistics grid is persistent (3 blocks per SM for fp32
+// members, 2 for bf16), so that the LCP grid runs beside each band's stream
+// rather than after it.
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
@@ -172,8 +173,17 @@ __device__ __forceinline__ void store_stats(const StatsWsParams& p, int64_t n, c
     }
 }
 
+// bf16 members (8-byte loads) take up to 80 registers a thread: 10 members per batch, so
+// that a 20-member ensemble streams in two round trips per chunk instead of three.
+template <typename T>
+struct StatsTune {
+    static constexpr int kMinBlocks = sizeof(T) == 2 ? 3 : 4;  // resident blocks per SM the registers allow
+    static constexpr int kBatch8 = 10;                          // members per batch of 8-byte loads
+    static constexpr int kPersist = sizeof(T) == 2 ? 2 : 3;     // persistent blocks per SM (several bands)
+};
+
 template <typename T, int VEC>
-__global__ void __launch_bounds__(kST, 4) stats_ws_kernel(const __grid_constant__ StatsWsParams p) {
+__global__ void __launch_bounds__(kST, StatsTune<T>::kMinBlocks) stats_ws_kernel(const __grid_constant__ StatsWsParams p) {
     const T* __restrict__ u = reinterpret_cast<const T*>(p.u);
     const T* __restrict__ v = reinterpret_cast<const T*>(p.v);
     const uint64_t pol = policy_evict_first();
@@ -205,7 +215,8 @@ __global__ void __launch_bounds__(kST, 4) stats_ws_kernel(const __grid_constant_
                     s2v[e] = fmaf(dv, dv, s2v[e]);
                 }
             };
-            constexpr int UNROLL = VEC >= 8 ? 4 : 8;  // 16 loads in flight per thread
+            // 16-byte loads: 8 members (16 loads) per batch; 8-byte loads: StatsTune's batch
+            constexpr int UNROLL = sizeof(typename L::raw_t) < 16 ? StatsTune<T>::kBatch8 : 8;
             int m = 1;
             if (sizeof(typename L::raw_t) < 16 && M >= UNROLL) {
                 // 8-byte loads: member 0 (the shift) travels with members 1 .. UNROLL-1, one round
@@ -962,12 +973,14 @@ lcp_status run(const void* u, const void* v, int M, int H, int W, int64_t stride
         sp.mplane = (int64_t)Hc * sp.mwords;
         const int64_t groups = (sp.n_end - sp.n_begin + VEC - 1) / VEC;
         int64_t grid = (groups + kST - 1) / kST;  // one chunk per block
-        // Several bands: a persistent grid of 3 blocks per SM (chunks in vertex order),
-        // so that every block is resident at once, the dependent LCP grid launches
-        // at the start and its blocks run beside the stream on the SM space left
-        // over, instead of after the band's last wave (measured: 8192^2 bf16 K = 4,
-        // 2.68 -> 2.54 ms; a single band is faster with one chunk per block).
-        if (L.band_rows < Hc) grid = std::min<int64_t>(grid, (int64_t)num_sms() * 3);
+        // Several bands: a persistent grid (chunks in vertex order) of StatsTune's
+        // blocks per SM, so that every block is resident at once, the dependent LCP
+        // grid launches at the start and its blocks run beside the stream on the
+        // registers left over, instead of after the band's last wave (measured, 8192^2
+        // bf16 K = 4: 2.68 -> 2.54 ms with 3 blocks of 64 registers; 2.52 -> 2.30 ms
+        // with 2 blocks of 80 registers and 10-member batches, which leave room for
+        // two LCP blocks per SM; a single band is faster with one chunk per block).
+        if (L.band_rows < Hc) grid = std::min<int64_t>(grid, (int64_t)num_sms() * StatsTune<T>::kPersist);
         stats_ws_kernel<T, VEC><<<(unsigned)grid, kST, 0, st>>>(sp);
         lcp_status s = check_launch("lcp_fused_ws (statistics)");
         if (s != LCP_OK) return s;

@@ -1,6 +1,6 @@
 """GPU parity: every C-ABI entry point against the FP64 oracle on the same inputs.
 
-Tolerances (stated here, derived in the design doc):
+Tolerances (each derived from the arithmetic of the two sides):
 * LCP in fp32: max |gpu - oracle| <= 1e-5 (the target), observed ~1e-6.
 * LCP in fp16: |gpu - fp16(oracle)| <= 1 fp16 ulp of the value.
 * Mean-field masks: bit-exact on dyadic data (exact arithmetic on both sides);
