@@ -754,27 +754,17 @@ def learned_arm(args):
         if evs:
             evs[2].record(stream)
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local).start()
-    time.sleep(0.35)
     n = args.steps
+    # the timed region: a run of n-step blocks long enough for the clock sampler (median block)
+    block_ms, blk, clk = timed_blocks(torch, step, n, args.warmup, local, pg, dev)
+    ms_per_step = block_ms / n
+    # the per-kernel split of the step (rooflines of the two kernels): one more run of n
+    # steps with an event between the moments kernel and the network
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n)]
-    if pg:
-        torch.distributed.barrier()
     torch.cuda.synchronize()
-    t_wall0 = time.time()
     for i in range(n):
         step(ev[i])
     torch.cuda.synchronize()
-    t_wall1 = time.time()
-    if pg:
-        torch.distributed.barrier()
-    time.sleep(0.25)
-    clocks.stop()
-    total_ms = max_over_ranks(ev[0][0].elapsed_time(ev[-1][2]), device=dev)
-    ms_per_step = total_ms / n
     mom_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / n
     inf_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / n
     value = weak_scaling_value(Hc * Wc, world, ms_per_step)
@@ -887,9 +877,10 @@ def learned_arm(args):
             "dtype": "f32 moments, bf16 network", "data": "synthetic",
             "config": {"workload": LEARNED_WORKLOAD, "H": Hh, "W": Ww, "M": Mm, "K": Kk, "global_batch": world,
                        "parallelism": f"independent fields x{world}" if world > 1 else "single",
-                       "l2": "no flush: inputs 419 MB > 129 MB L2", "lcp_values_per_s": value * Kk},
+                       "l2": "no flush: inputs 419 MB > 129 MB L2", "lcp_values_per_s": value * Kk,
+                       "timing": blk},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "accuracy": acc,
-            "clocks": clocks.summary(t_wall0, t_wall1), "gpu_launches": 2 * n,
+            "clocks": clk, "gpu_launches": 2 * n * blk["blocks"],
             "gpu": torch.cuda.get_device_name(dev),
         }
         print(json.dumps(line), flush=True)

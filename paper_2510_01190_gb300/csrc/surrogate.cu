@@ -173,6 +173,29 @@ __device__ __forceinline__ CellPart cell_part(const float4 (&k)[4]) {
     return p;
 }
 
+// below_above for two vertices at once: the same steps per vertex, the erfc
+// polynomial on paired FP32 instructions (each half one IEEE operation, so the
+// results equal two scalar calls bit for bit).
+__device__ __forceinline__ void below_above2(const VertexG& g0, const VertexG& g1, float c, float (&p)[2],
+                                             float (&q)[2]) {
+    const float2 t = __fmul2_rn(__fadd2_rn(make_float2(g0.mu, g1.mu), make_float2(-c, -c)), make_float2(g0.s, g1.s));
+    const float2 e = half_erfc_nonneg2(make_float2(fabsf(t.x), fabsf(t.y)));
+    const float tt[2] = {t.x, t.y}, ee[2] = {e.x, e.y}, ss[2] = {g0.s, g1.s}, mm[2] = {g0.mu, g1.mu};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (ss[k] == 0.0f) {
+            p[k] = (mm[k] < c) ? 1.0f : 0.0f;
+            q[k] = 1.0f - p[k];
+        } else if (tt[k] >= 0.0f) {
+            p[k] = ee[k];
+            q[k] = 1.0f - ee[k];
+        } else {
+            q[k] = ee[k];
+            p[k] = 1.0f - ee[k];
+        }
+    }
+}
+
 // The network's prior: the logit of the independent-Gaussian LCP, clamped to
 // [1e-6, 1 - 1e-6] (|logit| <= 13.8); the output layer adds it to its own sum.
 __device__ __forceinline__ float prior_logit(float g) {
@@ -194,10 +217,15 @@ __device__ __forceinline__ float cell_feature_words(const CellPart& p, float c, 
         f[4 * v + 1] = p.ratio[v];
         f[4 * v + 2] = p.skew[v];
         f[4 * v + 3] = p.kurt[v];
-        float pv, qv;
-        below_above(p.g[v], c, pv, qv);
-        pb *= pv;
-        qb *= qv;
+    }
+#pragma unroll
+    for (int v = 0; v < 4; v += 2) {  // the four vertices' (p, q) as two paired erfc evaluations
+        float pv[2], qv[2];
+        below_above2(p.g[v], p.g[v + 1], c, pv, qv);
+        pb *= pv[0];
+        qb *= qv[0];
+        pb *= pv[1];
+        qb *= qv[1];
     }
     f[16] = 1.f - pb - qb;
 #pragma unroll
@@ -459,8 +487,11 @@ __global__ void __launch_bounds__(kMT, kTcCtasPerSm) mlp_infer_tc_kernel(const f
                 tmem_ld16(lane_base + 16 * cg, z);
                 uint32_t hw[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    hw[e] = tanh_bf16x2(z[2 * e] + S.b1[16 * cg + 2 * e], z[2 * e + 1] + S.b1[16 * cg + 2 * e + 1]);
+                for (int e = 0; e < 8; ++e) {  // bias added two units at a time (paired FP32 add)
+                    const float2 zz = __fadd2_rn(make_float2(z[2 * e], z[2 * e + 1]),
+                                                 *reinterpret_cast<const float2*>(&S.b1[16 * cg + 2 * e]));
+                    hw[e] = tanh_bf16x2(zz.x, zz.y);
+                }
                 *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(S.A) + canon_off(t, 16 * cg, kHid / 8)) =
                     make_uint4(hw[0], hw[1], hw[2], hw[3]);
                 *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(S.A) + canon_off(t, 16 * cg + 8, kHid / 8)) =
@@ -488,8 +519,9 @@ __global__ void __launch_bounds__(kMT, kTcCtasPerSm) mlp_infer_tc_kernel(const f
                 tmem_ld16(lane_base + 16 * cg, z);
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    const float2 h = unpack_bf16(
-                        tanh_bf16x2(z[2 * e] + S.b2[16 * cg + 2 * e], z[2 * e + 1] + S.b2[16 * cg + 2 * e + 1]));
+                    const float2 zz = __fadd2_rn(make_float2(z[2 * e], z[2 * e + 1]),
+                                                 *reinterpret_cast<const float2*>(&S.b2[16 * cg + 2 * e]));
+                    const float2 h = unpack_bf16(tanh_bf16x2(zz.x, zz.y));
                     z3 = fmaf(h.x, S.w3[16 * cg + 2 * e], fmaf(h.y, S.w3[16 * cg + 2 * e + 1], z3));
                 }
             }
