@@ -1078,6 +1078,7 @@ def timed_blocks(torch, step, k, warmup, local, pg, dev, min_seconds=0.5, max_bl
     per = sorted(evs[b].elapsed_time(evs[b + 1]) for b in range(blocks))
     med = float(np.median(per))
     stats = {"blocks": blocks, "steps_per_block": k, "block_ms_median": round(med, 5),
+             "block_ms_mean": round(float(np.mean(per)), 5),
              "block_ms_min": round(per[0], 5), "block_ms_max": round(per[-1], 5),
              "timed_region_s": round(t1 - t0, 3)}
     return max_over_ranks(med, device=dev), stats, clocks.summary(t0, t1)
