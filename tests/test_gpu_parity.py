@@ -406,6 +406,31 @@ def test_fused_ws_row_bands_match_oracle(lib):
     assert np.array_equal(lib.unpack_mask(mask, w).cpu().numpy()[guard], ref["mask"][guard])
 
 
+@pytest.mark.parametrize("m", [2, 9, 10, 11, 20, 23, 31])
+def test_fused_ws_bf16_banded_member_batches(lib, m):
+    """bf16 members run in several row bands (a small workspace), so the statistics
+    grid is the persistent one, with member counts that give every batch shape of the
+    8-byte loads: fewer members than a batch, exactly one batch, a batch plus a
+    remainder, two batches, two plus a remainder.  Against the oracle on the same
+    bf16-rounded values, masks outside the guard band, and bit for bit against the
+    single-band call (the per-vertex records do not depend on the bands)."""
+    h, w = 120, 256
+    d = _fields(h, w, m, seed=40 + m, k=4)
+    u16, v16 = _dev(d["u"], torch.bfloat16), _dev(d["v"], torch.bfloat16)
+    iso = d["isovalues"]
+    row_bytes = 2 * w * 16
+    ws = torch.empty(40 * row_bytes + 1024, dtype=torch.uint8, device="cuda")
+    ws = ws[(256 - ws.data_ptr() % 256) % 256:]
+    assert lib.lcp_fused_band_rows(h, w, ws.numel()) < h - 1  # several bands
+    got, got_mask = lib.lcp_fused_ws(u16, v16, iso, mask=True, workspace=ws)
+    one, one_mask = lib.lcp_fused_ws(u16, v16, iso, mask=True)
+    assert torch.equal(got, one) and torch.equal(got_mask, one_mask)
+    ref = O.lcp_closed_form(_np(u16), _np(v16), 1.0, 1.0, iso)
+    assert np.max(np.abs(_np(got) - ref["lcp"])) <= LCP_TOL
+    guard = _oracle_mask_guard(ref["mu_d"], iso)
+    assert np.array_equal(lib.unpack_mask(got_mask, w).cpu().numpy()[guard], ref["mask"][guard])
+
+
 @pytest.mark.slow
 def test_fused_ws_ocean_8192_bf16_sampled(lib):
     """The 8192 x 8192 ocean-shaped workload (20 bf16 members, K = 4: 5.4 GB of
