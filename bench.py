@@ -944,6 +944,19 @@ def ocean_arm(args):
                                  Hh, Ww, iso, [(0, min(Hh, 24), 0, cw), (Hh // 2 - 12, Hh // 2 + 12, Ww - cw, Ww),
                                                (Hh - min(Hh, 24), Hh, Ww // 2 - cw // 2, Ww // 2 + cw // 2)])
     peak, peak_kind = measured_hbm_peak()
+    # The statistics pass on its own: the unfused call lcp_stats on the same members (mean and
+    # variance of u and v written to HBM as four fp32 planes), timed the same way after the
+    # step's timed region; every rank times its own field.
+    souts = tuple(torch.empty((Hh, Ww), dtype=torch.float32, device=dev) for _ in range(4))
+    s_ms, s_blk, s_clk = timed_blocks(torch, lambda: lib.lcp_stats(u, v, 1, out=souts), n, args.warmup, local, pg, dev)
+    s_bytes = 2 * Mm * Hh * Ww * 2 + 4 * Hh * Ww * 4
+    s_kern = s_blk["block_ms_median"] / n
+    stats_pass = {"call": "lcp_stats", "kernel": "stats_bf16x4_kernel", "ms": round(s_ms / n, 4),
+                  "alg_bytes": s_bytes, "achieved": round(s_bytes / (s_kern / 1e3) / 1e9, 1), "peak": peak,
+                  "unit": "GB/s", "frac": round(s_bytes / (s_kern / 1e3) / 1e9 / peak, 4), "peak_kind": peak_kind,
+                  "timing": s_blk, "clocks": s_clk,
+                  "traffic": profiled_traffic("lcp_stats_ocean_8192_m20_bf16.md", ("stats.cu", "lcp_common.cuh"))}
+    del souts
     achieved = alg / (kern_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4),
@@ -976,7 +989,7 @@ def ocean_arm(args):
                        "l2": f"no flush: inputs {2 * Mm * Hh * Ww * 2 / 1e9:.1f} GB > 129 MB L2", "timing": blk,
                        "lcp_values_per_s": value * Kk,
                        "hbm_frac_of_measured": roof["frac"]},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": None, "accuracy": accuracy,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": None, "accuracy": accuracy, "stats_pass": stats_pass,
             "e2e_note": "not measured for this line: 5.4 GB of members per step would be pinned on the host",
             "clocks": clk, "gpu_launches": 2 * ws_row_bands(lib, Mm, Hh, Ww) * n * blk["blocks"],
             "gpu": torch.cuda.get_device_name(dev),

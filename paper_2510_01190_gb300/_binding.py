@@ -243,10 +243,18 @@ def _plane(t, h, w, name):
         raise ValueError(f"{name} must be a contiguous float32 CUDA tensor [{h}, {w}]")
 
 
-def lcp_stats(u, v, ddof: int = 1):
-    """Per-vertex (mean, variance) of u and v over the members (Sec. 3.1)."""
+def lcp_stats(u, v, ddof: int = 1, out=None):
+    """Per-vertex (mean, variance) of u and v over the members (Sec. 3.1):
+    (mu_u, var_u, mu_v, var_v), written into `out` (four fp32 [H][W] planes) when given."""
     m, h, w, stride = _members(u, v)
-    outs = [torch.empty((h, w), dtype=torch.float32, device=u.device) for _ in range(4)]
+    if out is None:
+        outs = [torch.empty((h, w), dtype=torch.float32, device=u.device) for _ in range(4)]
+    else:
+        outs = list(out)
+        if len(outs) != 4:
+            raise ValueError("lcp_stats: out must hold four planes (mu_u, var_u, mu_v, var_v)")
+        for t, n in zip(outs, ("mu_u", "var_u", "mu_v", "var_v")):
+            _plane(t, h, w, n)
     lib = load()
     _check(lib.lcp_stats(_ptr(u), _ptr(v), _dtype_code(u.dtype), m, h, w, stride, ddof, *map(_ptr, outs), _stream()))
     return tuple(outs)

@@ -81,6 +81,21 @@ def test_stats_bf16_and_strided_members(lib):
         assert np.max(np.abs(_np(var_u) - ov) / (ov + 1e-12)) < 2e-5
 
 
+@pytest.mark.parametrize("m", [1, 2, 9, 10, 11, 20, 23, 31])
+def test_stats_bf16_member_batches(lib, m):
+    """bf16 lcp_stats over member counts that give every batch shape of its 8-byte
+    loads (below one batch, exactly one, one plus a remainder, two, two plus a
+    remainder), on a plane whose vertex count leaves a ragged tail (37 x 53 = 1961)."""
+    ddof = 0 if m == 1 else 1
+    d = _fields(37, 53, m, seed=70 + m)
+    u16, v16 = _dev(d["u"], torch.bfloat16), _dev(d["v"], torch.bfloat16)
+    mu_u, var_u, mu_v, var_v = lib.lcp_stats(u16, v16, ddof)
+    for x, mu, var in ((u16, mu_u, var_u), (v16, mu_v, var_v)):
+        om, ov = O.ensemble_stats(_np(x), ddof)  # the same bf16-rounded values
+        assert np.max(np.abs(_np(mu) - om) / (np.abs(om) + np.sqrt(ov) + 1e-30)) < 2e-6
+        assert np.max(np.abs(_np(var) - ov) / (ov + 1e-12)) < 2e-5
+
+
 @pytest.mark.parametrize("h,w,dx,dy", [(64, 64, 1.0, 1.0), (9, 130, 0.5, 2.0), (2, 2, 1.0, 3.0), (300, 7, 0.1, 0.1)])
 def test_divergence_parity(lib, h, w, dx, dy):
     st = synth.random_stats(h * w, h, w, zero_fraction=0.05)
