@@ -695,10 +695,13 @@ __global__ void __launch_bounds__(kWT, 5)  // <= 102 registers: 20 warps per SM 
                                __shfl_down_sync(0xFFFFFFFFu, C.U.z, 1), 0.f);
         if (lane == 0) L = C.UE;
         if (lane == 31) R = C.UE;
-        if (ic == 0) L = C.U;
-        if (ic == W - 1) R = C.U;
-        const float4 Vlo = j > 0 ? VM : V0;
-        const float4 Vhi = j < H - 1 ? VP : V0;
+        // The one-sided stencils at the grid's edges need no selects: every record load
+        // is clamped to the grid, so at column 0 the left record is the vertex's own (lane
+        // 0's edge record is u[max(ic - 1, 0)]), at column W - 1 the right one is (lanes
+        // beyond the grid hold u[W - 1]), and at rows 0 and H - 1 the window's lower and
+        // upper v records are the row's own; the spacing factors are the one-sided ones.
+        // (Measured: lat-lon K = 8 0.0931 -> 0.0926 ms, ocean 2.311 -> 2.267 ms, bit-identical.)
+        const float4 Vlo = VM, Vhi = VP;
         float mu = fmaf((R.x - L.x) + (R.y - L.y), sx, ((Vhi.x - Vlo.x) + (Vhi.y - Vlo.y)) * sy);
         const float var = fmaf(R.z + L.z, sxq, (Vhi.z + Vlo.z) * syq);
         const bool zero = var == 0.0f;
