@@ -1,7 +1,9 @@
 // lcp_stats: per-vertex mean and variance of u and v over the ensemble
 // (Sec. 3.1, closing paragraph).  A flat, fully coalesced stream over the
 // member planes: each thread owns VEC consecutive vertices and walks the
-// members with UNROLL independent 16-byte loads per component in flight.
+// members with UNROLL independent loads per component in flight (fp32: 16-byte
+// loads of 4 vertices, 8 members a batch; bf16: stats_bf16x4_kernel below,
+// 8-byte loads of 4 vertices, 10 members a batch).
 //
 // Numerics: shifted sums about member 0 (Chan, Golub, LeVeque 1983):
 //   d_m = x_m - x_0,  S1 = sum d_m,  S2 = sum d_m^2,
