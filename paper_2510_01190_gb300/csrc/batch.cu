@@ -79,11 +79,31 @@ __device__ __forceinline__ void member_sums2(const T* __restrict__ u, const T* _
     const T* b[4] = {u + o0, v + o0, u + o1, v + o1};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        x0[q] = ldm(b[q]);
         s1[q] = 0.f;
         s2[q] = 0.f;
     }
     int m = 1;
+    if (M >= 8) {  // member 0 (the shift) travels with members 1 .. 7: one round trip fewer
+        float x[8][4];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[r][q] = ldm(b[q] + (int64_t)r * stride);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x0[q] = x[0][q];
+#pragma unroll
+        for (int r = 1; r < 8; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float d = x[r][q] - x0[q];
+                s1[q] += d;
+                s2[q] = fmaf(d, d, s2[q]);
+            }
+        m = 8;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x0[q] = ldm(b[q]);
+    }
     for (; m + 8 <= M; m += 8) {
         float x[8][4];
 #pragma unroll
