@@ -331,6 +331,39 @@ lcp_status lcp_batch_autotune(const lcp_batch_plan* plan, int reps, lcp_tune* be
                               lcp_stream_t stream);
 
 /*
+ * Autotuner cache (this library's addition; the paper has no counterpart): the
+ * tile lcp_batch_autotune picked, kept in a JSON file keyed by the batch's shape
+ * and the device, so that a later call or process takes it without timing every
+ * shape again.  The file holds {"lcp_tune_cache": 1, "entries": [{"key": ...,
+ * "tile": [rows, cols], "ms": [4 times]}, ...]}; it is rewritten whole on each
+ * store (a temporary file renamed over it).  A missing, empty or malformed file
+ * reads as empty.  All strings and pointers are HOST.
+ *
+ * lcp_tune_cache_lookup - the entry of `key` in the file at `path`: returns 1 and
+ *   fills *best (ctas_per_sm = 0) and ms (optional, 4 floats) on a hit, 0 on a
+ *   miss or an entry whose tile is not one of lcp_tune's shapes, LCP_ERR_ARG for
+ *   a NULL or empty path, a NULL key or best.  No device work.
+ * lcp_tune_cache_store - add or replace the entry of `key` (ms optional, else
+ *   zeros).  LCP_ERR_ARG for NULL arguments, a tile that is not one of the
+ *   shapes, or a file that cannot be written.  No device work.
+ * lcp_batch_tune_key - the key of a plan on the current device ("<device
+ *   name>|sm<SMs>|in<dtype>|out<dtype>|fields<n>|iso<n>|cells<n>|ciso<n>|
+ *   mbytes<n>") into buf (len bytes); returns its length, LCP_ERR_ARG when buf is
+ *   too small, LCP_ERR_CUDA without a device.
+ * lcp_batch_autotune_cached - the tile from the cache at cache_path (NULL: the
+ *   LCP_TUNE_CACHE environment variable; neither: no cache) when it holds the
+ *   plan's key (*from_cache = 1; no device work, so the plan's outputs are not
+ *   written), else lcp_batch_autotune (which writes them) and a store of the
+ *   result; ms (optional, 4 floats) as lcp_batch_autotune's.  A store that fails
+ *   returns LCP_ERR_ARG with *best already valid.
+ */
+int lcp_tune_cache_lookup(const char* path, const char* key, lcp_tune* best, float* ms);
+lcp_status lcp_tune_cache_store(const char* path, const char* key, const lcp_tune* best, const float* ms);
+int lcp_batch_tune_key(const lcp_batch_plan* plan, char* buf, size_t len);
+lcp_status lcp_batch_autotune_cached(const lcp_batch_plan* plan, int reps, const char* cache_path,
+                                     lcp_tune* best, float* ms, int* from_cache, lcp_stream_t stream);
+
+/*
  * Learned surrogate for ensembles that are not Gaussian.  The paper mentions
  * neural surrogates only among related work (Sec. 2); the network, its
  * features and its training are this library's addition.  Under the empirical

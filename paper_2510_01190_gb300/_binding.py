@@ -36,6 +36,10 @@ __all__ = [
     "lcp_batch_prepare",
     "lcp_batch",
     "lcp_batch_autotune",
+    "lcp_batch_autotune_cached",
+    "lcp_batch_tune_key",
+    "lcp_tune_cache_lookup",
+    "lcp_tune_cache_store",
     "Batch",
     "lcp_mc",
     "lcp_philox_fill",
@@ -125,6 +129,11 @@ _SIGNATURES = {
                                   ctypes.c_size_t, c_vp, ctypes.POINTER(lcp_batch_plan)]),
     "lcp_batch": (c_int, [ctypes.POINTER(lcp_batch_plan), ctypes.POINTER(lcp_tune), c_vp]),
     "lcp_batch_autotune": (c_int, [ctypes.POINTER(lcp_batch_plan), c_int, ctypes.POINTER(lcp_tune), c_fp, c_vp]),
+    "lcp_tune_cache_lookup": (c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(lcp_tune), c_fp]),
+    "lcp_tune_cache_store": (c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(lcp_tune), c_fp]),
+    "lcp_batch_tune_key": (c_int, [ctypes.POINTER(lcp_batch_plan), ctypes.c_char_p, ctypes.c_size_t]),
+    "lcp_batch_autotune_cached": (c_int, [ctypes.POINTER(lcp_batch_plan), c_int, ctypes.c_char_p,
+                                          ctypes.POINTER(lcp_tune), c_fp, ctypes.POINTER(c_int), c_vp]),
     "lcp_exact_empirical": (c_int, [c_vp, c_vp, c_int, c_int, c_int, c_int, c_i64, c_double, c_double, c_fp, c_int,
                                     c_vp, c_vp, c_vp]),
     "lcp_contours_workspace_bytes": (ctypes.c_size_t, [c_int, c_int, c_int]),
@@ -755,6 +764,52 @@ def lcp_batch_autotune(plan: lcp_batch_plan, reps: int = 3, stream=None):
     return (best.tile_rows, best.tile_cols), [float(x) for x in ms]
 
 
+def _path_bytes(path):
+    return None if path is None else os.fsencode(path)
+
+
+def lcp_tune_cache_lookup(path, key: str):
+    """The cached (tile, ms) of ``key`` in the JSON tune cache at ``path``, or None."""
+    best = lcp_tune()
+    ms = (ctypes.c_float * len(TILE_SHAPES))()
+    r = load().lcp_tune_cache_lookup(_path_bytes(path), key.encode(), ctypes.byref(best), ctypes.cast(ms, c_fp))
+    if r < 0:
+        _check(r)
+    return ((best.tile_rows, best.tile_cols), [float(x) for x in ms]) if r == 1 else None
+
+
+def lcp_tune_cache_store(path, key: str, tile, ms=None):
+    """Add or replace ``key``'s entry (tile (rows, cols), optional 4 times) in the tune cache."""
+    best = lcp_tune(int(tile[0]), int(tile[1]), 0)
+    arr = None
+    if ms is not None:
+        if len(ms) != len(TILE_SHAPES):
+            raise ValueError(f"ms must hold {len(TILE_SHAPES)} times")
+        arr = ctypes.cast((ctypes.c_float * len(TILE_SHAPES))(*[float(x) for x in ms]), c_fp)
+    _check(load().lcp_tune_cache_store(_path_bytes(path), key.encode(), ctypes.byref(best), arr))
+
+
+def lcp_batch_tune_key(plan: lcp_batch_plan) -> str:
+    """The tune-cache key of ``plan`` on the current device."""
+    buf = ctypes.create_string_buffer(512)
+    n = load().lcp_batch_tune_key(ctypes.byref(plan), buf, len(buf))
+    if n < 0:
+        _check(n)
+    return buf.value.decode()
+
+
+def lcp_batch_autotune_cached(plan: lcp_batch_plan, reps: int = 3, cache_path=None, stream=None):
+    """lcp_batch_autotune through the JSON tune cache at ``cache_path`` (None: $LCP_TUNE_CACHE,
+    else no cache).  Returns ((rows, cols), [ms per shape], from_cache)."""
+    best = lcp_tune()
+    ms = (ctypes.c_float * len(TILE_SHAPES))()
+    hit = c_int(0)
+    _check(load().lcp_batch_autotune_cached(ctypes.byref(plan), int(reps), _path_bytes(cache_path), ctypes.byref(best),
+                                            ctypes.cast(ms, c_fp), ctypes.byref(hit),
+                                            stream if stream is not None else _stream()))
+    return (best.tile_rows, best.tile_cols), [float(x) for x in ms], bool(hit.value)
+
+
 class Batch:
     """Many fields evaluated by one persistent launch.
 
@@ -794,8 +849,13 @@ class Batch:
         lcp_batch(self.plan, tune)
         return self.lcp, self.mask
 
-    def autotune(self, reps: int = 3):
-        return lcp_batch_autotune(self.plan, reps)
+    def autotune(self, reps: int = 3, cache_path=None):
+        """The fastest tile shape and every shape's time; with ``cache_path`` (or
+        $LCP_TUNE_CACHE) through the JSON tune cache (a hit times nothing)."""
+        if cache_path is None and not os.environ.get("LCP_TUNE_CACHE"):
+            return lcp_batch_autotune(self.plan, reps)
+        tile, ms, _ = lcp_batch_autotune_cached(self.plan, reps, cache_path)
+        return tile, ms
 
 
 def unpack_mask(mask_words, w: int):

@@ -127,6 +127,31 @@ def test_batch_dyadic_zero_variance_is_bit_exact(lib):
         assert np.array_equal(_np(l), ref["lcp"])
 
 
+def test_batch_autotune_through_the_json_cache(lib, tmp_path):
+    """The first cached autotune times every shape and records the result under the
+    plan's key; the second takes it from the file without timing; a batch of another
+    shape misses; the tile from the cache gives the oracle's maps."""
+    fields = _small_fields()
+    path = tmp_path / "tune.json"
+    b = lib.Batch(fields)
+    tile1, ms1, hit1 = lib.lcp_batch_autotune_cached(b.plan, 2, path)
+    assert not hit1 and tuple(tile1) in lib.TILE_SHAPES and min(ms1) > 0
+    key = lib.lcp_batch_tune_key(b.plan)
+    assert lib.lcp_tune_cache_lookup(path, key)[0] == tuple(tile1)
+    tile2, ms2, hit2 = lib.lcp_batch_autotune_cached(b.plan, 2, path)
+    assert hit2 and tuple(tile2) == tuple(tile1) and ms2 == pytest.approx(ms1)
+    assert b.autotune(reps=2, cache_path=path) == (tuple(tile1), pytest.approx(ms1))
+    other = lib.Batch(fields[:2])
+    assert lib.lcp_batch_tune_key(other.plan) != key
+    assert not lib.lcp_batch_autotune_cached(other.plan, 2, path)[2]
+    for l in b.lcp:
+        l.fill_(float("nan"))
+    lcp, _ = b.run(tile2)
+    torch.cuda.synchronize()
+    for f, l in zip(fields, lcp):
+        _check_field(lib, f, l, None)
+
+
 def test_batch_graph_replay_and_autotune(lib):
     fields = _small_fields()
     b = lib.Batch(fields, mask=True)
